@@ -1,0 +1,153 @@
+"""Brute-force, cell-by-cell checker for the oracle (tiny inputs only).
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, never by the product path.
+
+It enumerates every cell of the weighted cubical complex of an image (vertex
+construction, Section 5) and evaluates the transforms from their definitions
+(Section 2.2) via the per-cell formulas of Lemma 2.1 with the signs restored:
+
+* ECT(xi, t)  = sum_P (-1)^dim P phi(P) [max_P xi <= t]
+* R(xi, t)    = sum_P phi(P) c_P(t),  c_P = (-1)^dim P if P lies in {xi = t},
+                (-1)^(dim P - 1) if min_P xi < t < max_P xi, 0 otherwise
+* int kappa R = sum_{dim P >= 1} (-1)^(dim P - 1) phi(P) (kbar(max_P xi) - kbar(min_P xi))
+
+(Lemma 2.1 as printed drops the (-1)^dim factors and takes min_P for the ECT; the
+versions above follow from chi of the relative interiors, Appendix B.)
+
+It also evaluates Delta^-(xi, x) straight from its definition in Section 3 -- the
+Euler characteristic of the cells of the star of x whose maximum of xi is reached
+at x -- for a concrete generic xi, without the box formula the oracle uses.
+"""
+from __future__ import annotations
+
+from itertools import product
+
+import numpy as np
+
+from .oracle import vertex_coords
+
+
+def cells(img: np.ndarray):
+    """All cells of the complex: list of (dim, phi, vertex linear indices)."""
+    img = np.asarray(img).astype(np.int64)
+    n = img.ndim
+    m = tuple(reversed(img.shape))            # m_0 fastest
+    strides = [1]
+    for k in range(1, n):
+        strides.append(strides[-1] * m[k - 1])
+    flat = img.reshape(-1)
+    out = []
+    for base in product(*[range(mk) for mk in m]):      # base[k] = i_k
+        for S in product((0, 1), repeat=n):
+            if any(base[k] + S[k] >= m[k] for k in range(n)):
+                continue
+            verts = []
+            for g in product((0, 1), repeat=n):
+                if any(g[k] > S[k] for k in range(n)):
+                    continue
+                verts.append(sum((base[k] + g[k]) * strides[k] for k in range(n)))
+            verts = np.array(verts, dtype=np.int64)
+            out.append((sum(S), int(flat[verts].min()), verts))
+    return out
+
+
+def vertex_dots(img: np.ndarray, xi) -> np.ndarray:
+    """<xi, x(v)> for every vertex, in linear order, canonical rounding."""
+    img = np.asarray(img)
+    n = img.ndim
+    m = tuple(reversed(img.shape))
+    N = int(np.prod(m))
+    idx = np.arange(N, dtype=np.int64)
+    s = None
+    rest = idx.copy()
+    for k in range(n):
+        ik = rest % m[k]
+        rest //= m[k]
+        p = np.float64(xi[k]) * vertex_coords(m[k])[ik]
+        s = p if s is None else s + p
+    return s
+
+
+def ect_brute(img, xi, t) -> np.ndarray:
+    s = vertex_dots(img, xi)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.zeros(t.shape, dtype=np.int64)
+    for dim, phi, verts in cells(img):
+        if phi == 0:
+            continue
+        hi = s[verts].max()
+        sgn = -1 if dim % 2 else 1
+        out += sgn * phi * (hi <= t).astype(np.int64)
+    return out
+
+
+def radon_brute(img, xi, t) -> np.ndarray:
+    s = vertex_dots(img, xi)
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    out = np.zeros(t.shape, dtype=np.int64)
+    for dim, phi, verts in cells(img):
+        if phi == 0:
+            continue
+        lo, hi = s[verts].min(), s[verts].max()
+        inside = (lo == t) & (hi == t)
+        across = (lo < t) & (t < hi)
+        sgn = -1 if dim % 2 else 1          # (-1)^dim; (-1)^(dim-1) = -sgn
+        out += phi * (sgn * inside.astype(np.int64) - sgn * across.astype(np.int64))
+    return out
+
+
+def integral_kappa_radon(img, xi, kbar) -> complex:
+    """int kappa(t) R(xi, t) dt, summed cell by cell (kbar = primitive of kappa)."""
+    s = vertex_dots(img, xi)
+    total = 0.0
+    for dim, phi, verts in cells(img):
+        if phi == 0 or dim == 0:
+            continue
+        lo, hi = s[verts].min(), s[verts].max()
+        sgn = 1 if dim % 2 else -1          # (-1)^(dim-1)
+        total = total + sgn * phi * (kbar(hi) - kbar(lo))
+    return total
+
+
+def lower_star_brute(img, xi) -> np.ndarray:
+    """Delta^-(xi, x) for every vertex x from the definition (Section 3).
+
+    For each cell P containing x with max_P xi attained at x (and only there, xi
+    being generic), add (-1)^dim P phi(P).
+    """
+    img = np.asarray(img)
+    N = img.size
+    s = vertex_dots(img, xi)
+    out = np.zeros(N, dtype=np.int64)
+    for dim, phi, verts in cells(img):
+        top = verts[np.argmax(s[verts])]
+        if np.count_nonzero(s[verts] == s[top]) != 1:
+            raise ValueError("direction is not generic on this complex")
+        out[top] += (-1 if dim % 2 else 1) * phi
+    return out
+
+
+def ht_by_quadrature(img, xi, kappa, order: int = 12) -> complex:
+    """HT in the paper's sign convention, -int kappa(t) R(xi, t) dt, by quadrature.
+
+    R(xi, .) is constant on the open intervals between consecutive distinct vertex
+    dot products; its value there is taken from the cell-by-cell ECT through
+    R(t) = ECT(xi, t) + ECT(-xi, -t) - chi, and kappa is integrated over each interval
+    with an ``order``-point Gauss-Legendre rule.  Needs no primitive of kappa.
+    """
+    xi = np.asarray(xi, dtype=np.float64)
+    s = np.unique(vertex_dots(img, xi))
+    if len(s) < 2:
+        return 0.0
+    mids = 0.5 * (s[:-1] + s[1:])
+    chi = int(ect_brute(img, xi, np.array([np.inf]))[0])
+    R = ect_brute(img, xi, mids) + ect_brute(img, -xi, -mids) - chi
+    nodes, weights = np.polynomial.legendre.leggauss(order)
+    total = 0.0
+    for lo, hi, r in zip(s[:-1], s[1:], R):
+        if r == 0:
+            continue
+        half = 0.5 * (hi - lo)
+        tq = lo + half * (nodes + 1.0)
+        total = total + r * half * np.sum(weights * kappa(tq))
+    return -total
