@@ -1,0 +1,200 @@
+/*
+ * topot.h -- C ABI of libtopot.so: topological integral transforms of images and
+ * volumes on one GPU (critical-point tables, Euler characteristic transform, Radon
+ * transform, hybrid transforms and their gradient).
+ *
+ * Method: Lebovici, Oudot, Passe, "Efficient computation of topological integral
+ * transforms" (SEA 2024, arXiv 2405.02256).  Each entry point names the passage that
+ * defines the operation it performs.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - An image with n in {2, 3} axes has lengths m_0 .. m_{n-1}, m_0 being the FASTEST
+ *   memory axis; every m_k >= 2.  Vertex v = (i_0, .., i_{n-1}) has linear index
+ *   i_0 + m_0 (i_1 + m_1 i_2).
+ * - Complex: "dual"/vertex construction (Section 5): pixels are vertices, a cube
+ *   exists iff all its vertices are pixels, and carries the minimum of their values.
+ * - Embedding (Section 4.1): x_k(i) = (2 i - (m_k - 1)) / (2 (m_k - 1)), in [-0.5, 0.5].
+ * - Orthant o in [0, 2^n): bit k set <=> eps_k = -1.  The sign vector of a direction
+ *   xi is eps_k = +1 if xi_k >= 0 (zero included), else -1 (Section 3, Lemma 3.2).
+ * - Dot products <xi, x(v)> and thresholds t_j = a + j (b - a) / (T - 1) (Appendix A.4)
+ *   are decided exactly as the FP64 expressions
+ *       s   = fl(fl(fl(xi_0 x_0) + fl(xi_1 x_1)) + fl(xi_2 x_2))
+ *       t_j = fl(a + fl(fl(j fl(b - a)) / (T - 1)))
+ *   would decide them; integer results (tables, ECT, Radon) are therefore exact.
+ * - Pointers named d_* are DEVICE pointers, h_* HOST pointers; the caller owns them.
+ *   `stream` is a cudaStream_t (NULL = legacy default stream).  Unless stated
+ *   otherwise calls only enqueue work on `stream` and return; outputs are valid once
+ *   the stream has reached that point.  Calls that use one tables handle must be
+ *   ordered on one stream (the handle owns a single workspace).
+ * - No exception crosses the ABI.  Every call returns a topot_status; on error the
+ *   outputs are unspecified and topot_last_error() gives a message (thread-local).
+ * - Directions must be finite.
+ */
+#ifndef TOPOT_H
+#define TOPOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TOPOT_API __attribute__((visibility("default")))
+#else
+#define TOPOT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TOPOT_OK = 0,
+    TOPOT_ERR_INVALID_ARG = 1,   /* bad shape, pointer, size or enum value          */
+    TOPOT_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement     */
+    TOPOT_ERR_OOM = 3,           /* device allocation failed                        */
+    TOPOT_ERR_CUDA = 4,          /* a CUDA runtime call failed                      */
+    TOPOT_ERR_OVERFLOW = 5,      /* a result would not fit its integer type          */
+    TOPOT_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up              */
+} topot_status;
+
+typedef enum { TOPOT_U8 = 0, TOPOT_I32 = 1 } topot_dtype;
+
+/* TOPOT_VERTEX: dual construction (Section 5).  TOPOT_TOP (one top cube per pixel,
+ * Section 4.1) is not implemented: TOPOT_ERR_UNSUPPORTED. */
+typedef enum { TOPOT_VERTEX = 0, TOPOT_TOP = 1 } topot_construction;
+
+/* Kernel primitives kbar of the hybrid transform (Section 2.2; Lemma 3.1):
+ *   LAPLACE  kbar(s) = e^s             (Appendix A.2 uses kbar = exp)
+ *   FOURIER  kbar(s) = sin s + i cos s (kappa(t) = e^{-i t}); output (re, im)
+ *   BESSEL   kbar(s) = J_0(s)          (kappa = -J_1)                          */
+typedef enum { TOPOT_LAPLACE = 0, TOPOT_FOURIER = 1, TOPOT_BESSEL = 2 } topot_kernel;
+
+/* FP32C: FP32 terms, Kahan-compensated per thread, FP64 cross-block combine
+ *        (Laplace evaluated as e^{M} e^{s - M}, M = sum_k |xi_k| / 2, so no term
+ *        overflows).  FP64: plain FP64 terms and sums. */
+typedef enum { TOPOT_FP32C = 0, TOPOT_FP64 = 1 } topot_precision;
+
+typedef struct topot_tables topot_tables;   /* opaque; owns the device tables */
+
+/* Tile shapes of the evaluation kernels; 0 = library default.  Set by the
+ * autotuner of the Python binding, or by hand. */
+typedef struct {
+    int ect_dirs_per_warp;    /* 8, 16 or 32 directions share one warp (ECT, Radon)  */
+    int ht_dirs_per_lane;     /* 1, 2 or 4 directions per lane (hybrid, FP32C)       */
+    int chunk;                /* critical points per work item (multiple of 256)     */
+    int ctas_per_sm;          /* resident blocks per SM of the persistent grids      */
+} topot_tuning;
+
+/* ---------------------------------------------------------------------------
+ * Critical tables (Section 3: Delta^-; Section 4.2: preprocessing)
+ * ---------------------------------------------------------------------------
+ * For each image b and orthant o, the table of classical critical values
+ *   Delta^-_o(v) = chi(phi restricted to LwSt(eps_o, v))
+ *               = sum over delta in {0,1}^n, box v..v - delta (.) eps existing,
+ *                 of (-1)^|delta| min(phi over the box)
+ * keeps every vertex with Delta^-_o(v) != 0, in ascending vertex index; and for
+ * each representative orthant r < 2^(n-1) the table of
+ *   Delta_r(v) = Delta^-_r(v) - Delta^-_{r ^ (2^n - 1)}(v)    (= -Delta^ord_r)
+ * (Delta_{-eps} = -Delta_eps).  chi(phi) = sum_v Delta^-_o(v) for any o.
+ *
+ * d_pixels : image data (uint8 or int32, see dtype); image b starts at element
+ *            h_offsets[b] and has h_shapes[b*n + k] = m_k.  Images must not alias
+ *            outputs.  int32 values must satisfy |phi| < 2^26.
+ * B        : number of images, >= 1.  n: 2 or 3.
+ * out      : receives a new handle; release it with free_tables().
+ * Synchronous: allocates, launches the extraction on `stream`, waits for it and
+ * reads the table sizes back.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA,
+ * OVERFLOW (int32 input out of range), TIMEOUT.
+ */
+TOPOT_API topot_status build_critical_tables(const void* d_pixels, topot_dtype dtype, int n,
+                                   const int64_t* h_shapes, const int64_t* h_offsets,
+                                   int B, topot_construction construction,
+                                   void* stream, topot_tables** out);
+
+/* Allocate a handle for images of the given shapes without launching anything.
+ * Same arguments as build_critical_tables minus the pixels and stream. */
+TOPOT_API topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes,
+                           const int64_t* h_offsets, int B,
+                           topot_construction construction, topot_tables** out);
+
+/* Enqueue the extraction of all tables of `t` from d_pixels on `stream`
+ * (asynchronous, no allocation, no host synchronisation: may be captured in a
+ * CUDA graph once the handle exists).  Table sizes stay on the device; the
+ * evaluation calls read them there.  tables_sync() makes them visible on the host. */
+TOPOT_API topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream);
+
+/* Wait for `stream`, read table sizes, chi and the device error word of `t`.
+ * Returns the first device-side error recorded since the last sync (OVERFLOW,
+ * TIMEOUT) and clears it. */
+TOPOT_API topot_status tables_sync(topot_tables* t, void* stream);
+
+/* Sizes of one table set after a sync: n_lower = |{v: Delta^-_o(v) != 0}|,
+ * n_delta = |{v: Delta_r(v) != 0}| with r the representative of o (the partner's
+ * table is the negation), chi = chi(phi) of image `image`. */
+TOPOT_API topot_status tables_info(const topot_tables* t, int image, int orthant,
+                         int64_t* n_lower, int64_t* n_delta, int64_t* chi);
+
+/* Copy one table to host memory (synchronous).  kind 0: Delta^-_orthant;
+ * kind 1: Delta_orthant (orthant must be a representative, < 2^(n-1)).
+ * h_idx / h_val need room for the size tables_info() reports. */
+TOPOT_API topot_status tables_copy_to_host(const topot_tables* t, int image, int orthant, int kind,
+                                 int32_t* h_idx, int32_t* h_val);
+
+/* Override the evaluation tile shapes of a handle (NULL restores defaults). */
+TOPOT_API topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning);
+
+TOPOT_API void free_tables(topot_tables* t);
+
+/* ---------------------------------------------------------------------------
+ * Transforms on a grid of directions x thresholds
+ * ---------------------------------------------------------------------------
+ * d_dirs : FP64 directions, [D][n] shared by every image (per_image_dirs = 0) or
+ *          [B][D][n] (per_image_dirs = 1).
+ * Thresholds t_j = a + j (b - a) / (T - 1), j < T, T >= 2, a = t_min, b = t_max.
+ * d_out  : int32 [B][D][T].
+ *
+ * ect (Lemma 3.1; Section 4.3; Appendix A.4 vectorisation):
+ *   ECT(xi, t_j) = sum over v with <xi, v> <= t_j of Delta^-_{eps(xi)}(v).
+ * radon (Section 2.2; additivity of the Euler integral, Appendix B):
+ *   R(xi, t_j) = chi({xi = t_j}) = ECT(xi, t_j) + ECT(-xi, -t_j) - chi(phi)
+ *             = sum_{s_v <= t_j} Delta^-_{o}(v) + sum_{s_v >= t_j} Delta^-_{o^(2^n-1)}(v) - chi
+ *   exact for every xi, generic or not.
+ * Errors: INVALID_ARG; OVERFLOW when the sum of |Delta^-| of an image reaches 2^31
+ * (checked on the host when the sizes are known, else recorded on the device and
+ * reported by tables_sync). */
+TOPOT_API topot_status ect(const topot_tables* t, const double* d_dirs, int D, int per_image_dirs,
+                 double t_min, double t_max, int T, int32_t* d_out, void* stream);
+TOPOT_API topot_status radon(const topot_tables* t, const double* d_dirs, int D, int per_image_dirs,
+                   double t_min, double t_max, int T, int32_t* d_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Hybrid transforms (Section 2.2; closed form and sign of Lemma 3.1)
+ * ---------------------------------------------------------------------------
+ *   HT(xi) = - sum_v Delta^ord_eps(v) kbar(<xi, v>) = sum_v Delta_eps(v) kbar(<xi, v>)
+ * (= -int kappa(t) R(xi, t) dt).  d_out: FP64 [B][D] (LAPLACE, BESSEL) or
+ * [B][D][2] (FOURIER: re, im).  Deterministic for a given tuning.
+ * Accuracy (FP32C): |HT - exact| <= 1e-6 sum_v |Delta kbar| for the documented
+ * ranges |<xi, v>| <= pi. */
+TOPOT_API topot_status hybrid_transform(const topot_tables* t, topot_kernel kernel,
+                              topot_precision precision, const double* d_dirs, int D,
+                              int per_image_dirs, double* d_out, void* stream);
+
+/* Adjoint: d_gdirs = sum over images and outputs of d_gout * d HT / d xi, with
+ *   d HT(xi) / d xi_k = sum_v Delta_eps(v) kappa(<xi, v>) x_k(v),  kappa = kbar'
+ * (Lemma 3.1 differentiated inside an orthant, where the tables are constant by
+ * Lemma 3.2).  d_gout is shaped like d_out of hybrid_transform; d_gdirs like d_dirs
+ * (FP64).  For FOURIER, gout = (g_re, g_im) and the result is
+ * g_re d Re/d xi + g_im d Im/d xi.  With per_image_dirs = 0 the gradients of all
+ * images are summed per direction. */
+TOPOT_API topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel,
+                                   topot_precision precision, const double* d_dirs, int D,
+                                   int per_image_dirs, const double* d_gout,
+                                   double* d_gdirs, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+TOPOT_API const char* topot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOPOT_H */

@@ -1,0 +1,291 @@
+"""Thin Python binding of libtopot.so (C ABI in include/topot.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.
+Tensors are PyTorch CUDA tensors (PyTorch provides device memory and streams); the
+library is loaded on first use and a missing library raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtopot.so")
+
+U8, I32 = 0, 1
+VERTEX, TOP = 0, 1
+KERNELS = {"laplace": 0, "fourier": 1, "bessel": 2}
+PRECISIONS = {"fp32c": 0, "fp64": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "OVERFLOW", 6: "TIMEOUT"}
+
+API_SYMBOLS = (
+    "build_critical_tables", "tables_create", "tables_build", "tables_sync", "tables_info",
+    "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
+    "hybrid_transform_grad", "topot_last_error",
+)
+
+
+class TopotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"topot {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("ect_dirs_per_warp", ctypes.c_int), ("ht_dirs_per_lane", ctypes.c_int),
+                ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtopot.so and declare the C signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtopot.so not found at {path}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i32, i64p, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "build_critical_tables": [vp, i32, i32, i64p, i64p, i32, i32, vp, pp],
+        "tables_create": [i32, i32, i64p, i64p, i32, i32, pp],
+        "tables_build": [vp, vp, vp],
+        "tables_sync": [vp, vp],
+        "tables_info": [vp, i32, i32, i64p, i64p, i64p],
+        "tables_copy_to_host": [vp, i32, i32, i32, vp, vp],
+        "tables_set_tuning": [vp, ctypes.POINTER(Tuning)],
+        "ect": [vp, vp, i32, i32, dp, dp, i32, vp, vp],
+        "radon": [vp, vp, i32, i32, dp, dp, i32, vp, vp],
+        "hybrid_transform": [vp, i32, i32, vp, i32, i32, vp, vp],
+        "hybrid_transform_grad": [vp, i32, i32, vp, i32, i32, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.free_tables.argtypes = [vp]
+    L.free_tables.restype = None
+    L.topot_last_error.argtypes = []
+    L.topot_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise TopotError(status, load().topot_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _i64(a) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int64).reshape(-1))
+    return (ctypes.c_int64 * len(a))(*a.tolist())
+
+
+def _dirs(dirs: torch.Tensor, n: int, B: int):
+    if dirs.dtype != torch.float64 or not dirs.is_cuda:
+        raise ValueError("directions must be a CUDA float64 tensor")
+    dirs = dirs.contiguous()
+    if dirs.dim() == 2 and dirs.shape[1] == n:
+        return dirs, dirs.shape[0], 0
+    if dirs.dim() == 3 and dirs.shape[0] == B and dirs.shape[2] == n:
+        return dirs, dirs.shape[1], 1
+    raise ValueError(f"directions must be [D, {n}] or [{B}, D, {n}]")
+
+
+@dataclass
+class ImageBatch:
+    """Images packed in one device buffer: pixels (flat), shapes [B][n] (m_0 fastest), offsets."""
+    pixels: torch.Tensor
+    shapes: np.ndarray
+    offsets: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.shapes.shape[1]
+
+    @property
+    def B(self) -> int:
+        return self.shapes.shape[0]
+
+
+def pack_images(images, device="cuda", align: int = 16) -> ImageBatch:
+    """Pack numpy images (C order, last axis = coordinate 0) into one device buffer.
+
+    Each image starts at a multiple of ``align`` elements so that row copies can use
+    16-byte aligned bulk transfers when the row length allows it.
+    """
+    images = [np.ascontiguousarray(im) for im in images]
+    dt = images[0].dtype
+    if dt not in (np.uint8, np.int32):
+        raise ValueError("images must be uint8 or int32")
+    n = images[0].ndim
+    shapes, offsets, pos = [], [], 0
+    for im in images:
+        if im.ndim != n or im.dtype != dt:
+            raise ValueError("all images need the same rank and dtype")
+        shapes.append(list(reversed(im.shape)))
+        offsets.append(pos)
+        pos += -(-im.size // align) * align
+    host = np.zeros(pos, dtype=dt)
+    for im, off in zip(images, offsets):
+        host[off:off + im.size] = im.reshape(-1)
+    pix = torch.from_numpy(host).to(device)
+    return ImageBatch(pix, np.array(shapes, dtype=np.int64), np.array(offsets, dtype=np.int64))
+
+
+class Tables:
+    """Critical-point tables of a batch of images (owns the device tables)."""
+
+    def __init__(self, handle, n: int, B: int, dtype: int, shapes, offsets):
+        self._h = handle
+        self.n, self.B, self.dtype = n, B, dtype
+        self.shapes = np.asarray(shapes)
+        self.offsets = np.asarray(offsets)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("tables already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            load().free_tables(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def build(self, pixels: torch.Tensor, stream=None):
+        """Re-extract the tables from new pixels of the same shapes (asynchronous)."""
+        _check(load().tables_build(self.handle, _ptr(pixels), _stream(stream)))
+
+    def sync(self, stream=None):
+        _check(load().tables_sync(self.handle, _stream(stream)))
+
+    def info(self, image: int, orthant: int):
+        nl, nd, chi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().tables_info(self.handle, image, orthant, ctypes.byref(nl), ctypes.byref(nd),
+                                  ctypes.byref(chi)))
+        return nl.value, nd.value, chi.value
+
+    def table(self, image: int, orthant: int, kind: int):
+        """(idx, val) of one table as int64 numpy arrays (kind 0: Delta^-, 1: Delta)."""
+        nl, nd, _ = self.info(image, orthant)
+        cnt = nl if kind == 0 else nd
+        idx = np.zeros(max(cnt, 1), dtype=np.int32)
+        val = np.zeros(max(cnt, 1), dtype=np.int32)
+        _check(load().tables_copy_to_host(self.handle, image, orthant, kind,
+                                          idx.ctypes.data_as(ctypes.c_void_p),
+                                          val.ctypes.data_as(ctypes.c_void_p)))
+        return idx[:cnt].astype(np.int64), val[:cnt].astype(np.int64)
+
+    def set_tuning(self, ect_dirs_per_warp=0, ht_dirs_per_lane=0, chunk=0, ctas_per_sm=0):
+        tu = Tuning(ect_dirs_per_warp, ht_dirs_per_lane, chunk, ctas_per_sm)
+        _check(load().tables_set_tuning(self.handle, ctypes.byref(tu)))
+
+
+def build_critical_tables(batch: ImageBatch, stream=None) -> Tables:
+    L = load()
+    dtype = U8 if batch.pixels.dtype == torch.uint8 else I32
+    h = ctypes.c_void_p()
+    _check(L.build_critical_tables(_ptr(batch.pixels), dtype, batch.n, _i64(batch.shapes), _i64(batch.offsets),
+                                   batch.B, VERTEX, _stream(stream), ctypes.byref(h)))
+    return Tables(h, batch.n, batch.B, dtype, batch.shapes, batch.offsets)
+
+
+def tables_create(shapes, offsets, dtype=U8) -> Tables:
+    shapes = np.asarray(shapes, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(load().tables_create(dtype, shapes.shape[1], _i64(shapes), _i64(offsets), shapes.shape[0], VERTEX,
+                                ctypes.byref(h)))
+    return Tables(h, shapes.shape[1], shapes.shape[0], dtype, shapes, offsets)
+
+
+def ect(tables: Tables, dirs: torch.Tensor, t_min: float, t_max: float, T: int, out=None, stream=None):
+    """ECT(xi_d, t_j) for every image: int32 [B, D, T]."""
+    L = load()
+    dirs, D, per = _dirs(dirs, tables.n, tables.B)
+    if out is None:
+        out = torch.empty((tables.B, D, T), dtype=torch.int32, device=dirs.device)
+    _check(L.ect(tables.handle, _ptr(dirs), D, per, float(t_min), float(t_max), int(T), _ptr(out), _stream(stream)))
+    return out
+
+
+def radon(tables: Tables, dirs: torch.Tensor, t_min: float, t_max: float, T: int, out=None, stream=None):
+    """Radon transform R(xi_d, t_j) for every image: int32 [B, D, T]."""
+    L = load()
+    dirs, D, per = _dirs(dirs, tables.n, tables.B)
+    if out is None:
+        out = torch.empty((tables.B, D, T), dtype=torch.int32, device=dirs.device)
+    _check(L.radon(tables.handle, _ptr(dirs), D, per, float(t_min), float(t_max), int(T), _ptr(out),
+                   _stream(stream)))
+    return out
+
+
+def hybrid_transform(tables: Tables, kernel: str, dirs: torch.Tensor, precision: str = "fp32c", out=None,
+                     stream=None):
+    """HT(xi_d) per image: float64 [B, D] (Fourier: [B, D, 2] = (re, im))."""
+    L = load()
+    dirs, D, per = _dirs(dirs, tables.n, tables.B)
+    shape = (tables.B, D, 2) if kernel == "fourier" else (tables.B, D)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=dirs.device)
+    _check(L.hybrid_transform(tables.handle, KERNELS[kernel], PRECISIONS[precision], _ptr(dirs), D, per,
+                              _ptr(out), _stream(stream)))
+    return out
+
+
+def hybrid_transform_grad(tables: Tables, kernel: str, dirs: torch.Tensor, gout: torch.Tensor,
+                          precision: str = "fp32c", out=None, stream=None):
+    """sum over outputs of gout * dHT/dxi, shaped like dirs (float64)."""
+    L = load()
+    dirs, D, per = _dirs(dirs, tables.n, tables.B)
+    gout = gout.contiguous().to(torch.float64)
+    if out is None:
+        out = torch.empty_like(dirs)
+    _check(L.hybrid_transform_grad(tables.handle, KERNELS[kernel], PRECISIONS[precision], _ptr(dirs), D, per,
+                                   _ptr(gout), _ptr(out), _stream(stream)))
+    return out
+
+
+class HybridTransform(torch.autograd.Function):
+    """HT as a differentiable function of the directions (adjoint kernel in backward)."""
+
+    @staticmethod
+    def forward(ctx, dirs, tables, kernel, precision):
+        ctx.tables, ctx.kernel, ctx.precision = tables, kernel, precision
+        ctx.save_for_backward(dirs)
+        return hybrid_transform(tables, kernel, dirs.detach(), precision)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (dirs,) = ctx.saved_tensors
+        g = hybrid_transform_grad(ctx.tables, ctx.kernel, dirs.detach(), gout, ctx.precision)
+        return g, None, None, None

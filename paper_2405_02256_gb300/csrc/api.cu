@@ -1,0 +1,557 @@
+// C ABI of libtopot (declared in include/topot.h): validation, handle and workspace
+// management, and the launch sequences of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "eval_common.cuh"
+
+namespace topot {
+cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st);
+int extract_block(int n);
+int extract_k(int n);
+size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
+size_t hist_smem_bytes(int td, int T);
+cudaError_t launch_hist(const EvalPlan& P, const TablesDev& t, int td, int32_t* lo, int32_t* hi, int grid,
+                        cudaStream_t st);
+cudaError_t launch_hist_finish(int mode, int B, int D, int T, const long long* chi, int32_t* out,
+                               const int32_t* hi, cudaStream_t st);
+cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
+                      int grid, double* part, cudaStream_t st);
+cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
+                              const double* part, double* out, cudaStream_t st);
+cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
+                                  const double* part, const double* gout, double* gdirs, cudaStream_t st);
+}  // namespace topot
+
+using namespace topot;
+
+struct topot_tables {
+    int n = 0, B = 0, NO = 0, S = 0;
+    topot_dtype dtype = TOPOT_U8;
+    int device = 0, sm_count = 0;
+    std::vector<ImgDesc> h_img;
+    long long total_entries = 0;
+    long long num_tiles = 0;
+    int row_stride = 0, stage_rows = 0;
+    // device memory
+    void* meta = nullptr;             // one block: img, seg_count, chi, absum, err, ticket, status
+    ImgDesc* d_img = nullptr;
+    long long* seg_count = nullptr;
+    long long* chi = nullptr;
+    long long* absum = nullptr;
+    unsigned* err = nullptr;
+    unsigned* ticket = nullptr;
+    unsigned long long* status = nullptr;
+    size_t clear_bytes = 0;           // bytes from `chi` to the end of `status` zeroed per build
+    int* arena_idx = nullptr;
+    void* arena_val = nullptr;
+    // host copies (valid after tables_sync)
+    bool host_valid = false;
+    std::vector<long long> h_seg_count, h_chi, h_absum;
+    // evaluation workspace, grown on demand
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    topot_tuning tuning{};
+
+    TablesDev dev() const {
+        TablesDev t;
+        t.n = n;
+        t.B = B;
+        t.S = S;
+        t.val_bytes = dtype == TOPOT_U8 ? 2 : 4;
+        t.img = d_img;
+        t.arena_idx = arena_idx;
+        t.arena_val = arena_val;
+        t.seg_count = seg_count;
+        t.chi = chi;
+        t.absum = absum;
+        t.err = err;
+        return t;
+    }
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+topot_status fail(topot_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+topot_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(e == cudaErrorMemoryAllocation ? TOPOT_ERR_OOM : TOPOT_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define TOPOT_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+topot_status ensure_ws(topot_tables* t, size_t bytes) {
+    if (t->ws_bytes >= bytes) return TOPOT_OK;
+    if (t->ws) {
+        cudaError_t e = cudaFree(t->ws);
+        t->ws = nullptr;
+        t->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    const size_t sz = align_up(bytes + bytes / 4, 1 << 20);
+    cudaError_t e = cudaMalloc(&t->ws, sz);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    t->ws_bytes = sz;
+    return TOPOT_OK;
+}
+
+// Carves a workspace into aligned pieces.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool valid_dirs_args(const topot_tables* t, const void* d_dirs, int D, int per_image_dirs) {
+    return t && d_dirs && D >= 1 && (per_image_dirs == 0 || per_image_dirs == 1);
+}
+
+int hist_tile(const topot_tables* t, int D, int nsets_dirs_per_orthant, int T) {
+    int td = t->tuning.ect_dirs_per_warp;
+    if (td != 8 && td != 16 && td != 32) {
+        td = 32;
+        const int per_orthant = nsets_dirs_per_orthant;
+        if (per_orthant < 24) td = 16;
+        if (per_orthant < 12) td = 8;
+    }
+    (void)D;
+    while (td > 8 && hist_smem_bytes(td, T) > 200 * 1024) td >>= 1;
+    return td;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* topot_last_error(void) { return g_last_error.c_str(); }
+
+topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, const int64_t* h_offsets, int B,
+                           topot_construction construction, topot_tables** out) {
+    if (!out) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: out is NULL");
+    *out = nullptr;
+    if (construction == TOPOT_TOP)
+        return fail(TOPOT_ERR_UNSUPPORTED, "tables_create: top-dimensional construction is not implemented");
+    if (construction != TOPOT_VERTEX) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad construction");
+    if (dtype != TOPOT_U8 && dtype != TOPOT_I32) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad dtype");
+    if (n != 2 && n != 3) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: n must be 2 or 3");
+    if (B < 1 || !h_shapes || !h_offsets) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad image list");
+
+    topot_tables* t = new (std::nothrow) topot_tables();
+    if (!t) return fail(TOPOT_ERR_OOM, "tables_create: host allocation failed");
+    t->n = n;
+    t->B = B;
+    t->dtype = dtype;
+    t->NO = 1 << n;
+    t->S = t->NO + t->NO / 2;
+    cudaError_t e = cudaGetDevice(&t->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device);
+    if (e != cudaSuccess) {
+        delete t;
+        return cuda_fail(e, "tables_create: device query");
+    }
+    const int elem = dtype == TOPOT_U8 ? 1 : 4;
+    const int pad = 16 / elem;
+    const int tile_v = extract_block(n) * extract_k(n);
+    const int NP = n == 3 ? 3 : 1;
+    const size_t smem_budget = 96 * 1024;
+    long long tiles = 0, entries = 0;
+    int max_w = 1, max_r = 1;
+    t->h_img.resize(B);
+    for (int b = 0; b < B; ++b) {
+        ImgDesc& I = t->h_img[b];
+        memset(&I, 0, sizeof(I));
+        long long N = 1;
+        for (int k = 0; k < 3; ++k) {
+            const long long m = k < n ? h_shapes[(long long)b * n + k] : 1;
+            if (k < n && (m < 2 || m > (1 << 24))) {
+                delete t;
+                return fail(TOPOT_ERR_INVALID_ARG, "tables_create: every axis needs 2 <= m_k <= 2^24");
+            }
+            I.m[k] = (int)m;
+            N *= m;
+        }
+        if (N >= (1ll << 31) || h_offsets[b] < 0) {
+            delete t;
+            return fail(TOPOT_ERR_INVALID_ARG, "tables_create: an image must have < 2^31 vertices and offset >= 0");
+        }
+        I.offset = h_offsets[b];
+        I.N = N;
+        I.seg_base = entries;
+        entries += N * t->S;
+        I.tile_begin = tiles;
+        const int m0 = I.m[0], m1 = I.m[1];
+        if (m0 <= tile_v) {
+            I.W = m0;
+            I.R = std::max(1, std::min(tile_v / m0, m1));
+            // the staged rows must fit the shared-memory budget
+            while (I.R > 1 && (size_t)NP * (I.R + 2) * align_up((size_t)(pad + m0 + 1), pad) * elem > smem_budget)
+                --I.R;
+        } else {
+            I.W = tile_v;
+            I.R = 1;
+        }
+        I.segs_per_row = (m0 + I.W - 1) / I.W;
+        I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
+        tiles += (long long)I.tiles_per_plane * I.m[2];
+        I.div0 = make_fastdiv((uint32_t)m0);
+        I.div1 = make_fastdiv((uint32_t)m1);
+        max_w = std::max(max_w, I.W);
+        max_r = std::max(max_r, I.R);
+    }
+    t->total_entries = entries;
+    t->num_tiles = tiles;
+    t->row_stride = (int)align_up((size_t)(pad + max_w + 1), pad);
+    t->stage_rows = max_r + 2;
+
+    // device allocations
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        off = align_up(off, 256);
+        const size_t o = off;
+        off += bytes;
+        return o;
+    };
+    const size_t o_img = place(sizeof(ImgDesc) * B);
+    const size_t o_cnt = place(sizeof(long long) * B * t->S);
+    const size_t o_err = place(sizeof(unsigned));
+    const size_t o_chi = place(sizeof(long long) * B);
+    const size_t o_abs = place(sizeof(long long) * B * t->NO);
+    const size_t o_tic = place(sizeof(unsigned));
+    const size_t o_sta = place(sizeof(unsigned long long) * tiles * t->S);
+    const size_t meta_bytes = off;
+    e = cudaMalloc(&t->meta, meta_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&t->arena_idx, sizeof(int) * (size_t)entries);
+    if (e == cudaSuccess) e = cudaMalloc(&t->arena_val, (size_t)(dtype == TOPOT_U8 ? 2 : 4) * (size_t)entries);
+    if (e != cudaSuccess) {
+        free_tables(t);
+        return cuda_fail(e, "tables_create: device allocation");
+    }
+    char* m = reinterpret_cast<char*>(t->meta);
+    t->d_img = reinterpret_cast<ImgDesc*>(m + o_img);
+    t->seg_count = reinterpret_cast<long long*>(m + o_cnt);
+    t->err = reinterpret_cast<unsigned*>(m + o_err);
+    t->chi = reinterpret_cast<long long*>(m + o_chi);
+    t->absum = reinterpret_cast<long long*>(m + o_abs);
+    t->ticket = reinterpret_cast<unsigned*>(m + o_tic);
+    t->status = reinterpret_cast<unsigned long long*>(m + o_sta);
+    t->clear_bytes = meta_bytes - o_chi;
+    e = cudaMemcpy(t->d_img, t->h_img.data(), sizeof(ImgDesc) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(t->seg_count, 0, o_chi - o_cnt);   // counts + error word
+    if (e != cudaSuccess) {
+        free_tables(t);
+        return cuda_fail(e, "tables_create: initialise metadata");
+    }
+    const size_t smem = extract_smem_bytes(n, elem, t->row_stride, t->stage_rows);
+    if (smem > 200 * 1024) {
+        free_tables(t);
+        return fail(TOPOT_ERR_UNSUPPORTED, "tables_create: rows too wide for the shared-memory stage");
+    }
+    *out = t;
+    return TOPOT_OK;
+}
+
+topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
+    if (!t || !d_pixels) return fail(TOPOT_ERR_INVALID_ARG, "tables_build: NULL argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    t->host_valid = false;
+    TOPOT_CUDA(cudaMemsetAsync(t->chi, 0, t->clear_bytes, st));
+    ExtractArgs a;
+    a.t = t->dev();
+    a.pixels = d_pixels;
+    a.num_tiles = t->num_tiles;
+    a.ticket = t->ticket;
+    a.status = t->status;
+    a.row_stride = t->row_stride;
+    a.stage_rows = t->stage_rows;
+    TOPOT_CUDA(launch_extract(t->n, t->dtype, a, st));
+    return TOPOT_OK;
+}
+
+topot_status tables_sync(topot_tables* t, void* stream) {
+    if (!t) return fail(TOPOT_ERR_INVALID_ARG, "tables_sync: NULL handle");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    TOPOT_CUDA(cudaStreamSynchronize(st));
+    t->h_seg_count.resize((size_t)t->B * t->S);
+    t->h_chi.resize(t->B);
+    t->h_absum.resize((size_t)t->B * t->NO);
+    unsigned err = 0;
+    TOPOT_CUDA(cudaMemcpy(t->h_seg_count.data(), t->seg_count, sizeof(long long) * t->B * t->S,
+                          cudaMemcpyDeviceToHost));
+    TOPOT_CUDA(cudaMemcpy(t->h_chi.data(), t->chi, sizeof(long long) * t->B, cudaMemcpyDeviceToHost));
+    TOPOT_CUDA(cudaMemcpy(t->h_absum.data(), t->absum, sizeof(long long) * t->B * t->NO, cudaMemcpyDeviceToHost));
+    TOPOT_CUDA(cudaMemcpy(&err, t->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) TOPOT_CUDA(cudaMemset(t->err, 0, sizeof(unsigned)));
+    t->host_valid = true;
+    if (err & kDevErrTimeout) return fail(TOPOT_ERR_TIMEOUT, "device-side wait timed out");
+    if (err & kDevErrOverflow)
+        return fail(TOPOT_ERR_OVERFLOW, "value out of range (int32 pixel |phi| >= 2^26 or ECT bound >= 2^31)");
+    return TOPOT_OK;
+}
+
+topot_status build_critical_tables(const void* d_pixels, topot_dtype dtype, int n, const int64_t* h_shapes,
+                                   const int64_t* h_offsets, int B, topot_construction construction, void* stream,
+                                   topot_tables** out) {
+    if (!out) return fail(TOPOT_ERR_INVALID_ARG, "build_critical_tables: out is NULL");
+    if (!d_pixels) return fail(TOPOT_ERR_INVALID_ARG, "build_critical_tables: d_pixels is NULL");
+    topot_tables* t = nullptr;
+    topot_status s = tables_create(dtype, n, h_shapes, h_offsets, B, construction, &t);
+    if (s != TOPOT_OK) return s;
+    s = tables_build(t, d_pixels, stream);
+    if (s == TOPOT_OK) s = tables_sync(t, stream);
+    if (s != TOPOT_OK) {
+        const std::string msg = g_last_error;
+        free_tables(t);
+        g_last_error = msg;
+        return s;
+    }
+    *out = t;
+    return TOPOT_OK;
+}
+
+topot_status tables_info(const topot_tables* t, int image, int orthant, int64_t* n_lower, int64_t* n_delta,
+                         int64_t* chi) {
+    if (!t) return fail(TOPOT_ERR_INVALID_ARG, "tables_info: NULL handle");
+    if (!t->host_valid) return fail(TOPOT_ERR_INVALID_ARG, "tables_info: call tables_sync after tables_build");
+    if (image < 0 || image >= t->B || orthant < 0 || orthant >= t->NO)
+        return fail(TOPOT_ERR_INVALID_ARG, "tables_info: image or orthant out of range");
+    const int rep = (orthant & (t->NO >> 1)) ? (orthant ^ (t->NO - 1)) : orthant;
+    const long long* c = t->h_seg_count.data() + (size_t)image * t->S;
+    if (n_lower) *n_lower = c[orthant];
+    if (n_delta) *n_delta = c[t->NO + rep];
+    if (chi) *chi = t->h_chi[image];
+    return TOPOT_OK;
+}
+
+topot_status tables_copy_to_host(const topot_tables* t, int image, int orthant, int kind, int32_t* h_idx,
+                                 int32_t* h_val) {
+    if (!t || !h_idx || !h_val) return fail(TOPOT_ERR_INVALID_ARG, "tables_copy_to_host: NULL argument");
+    if (!t->host_valid) return fail(TOPOT_ERR_INVALID_ARG, "tables_copy_to_host: call tables_sync first");
+    if (image < 0 || image >= t->B || orthant < 0 || orthant >= t->NO || (kind != 0 && kind != 1))
+        return fail(TOPOT_ERR_INVALID_ARG, "tables_copy_to_host: bad image, orthant or kind");
+    if (kind == 1 && orthant >= t->NO / 2)
+        return fail(TOPOT_ERR_INVALID_ARG, "tables_copy_to_host: Delta tables exist for orthants < 2^(n-1)");
+    const int seg = kind == 0 ? orthant : t->NO + orthant;
+    const ImgDesc& I = t->h_img[image];
+    const long long cnt = t->h_seg_count[(size_t)image * t->S + seg];
+    const long long base = I.seg_base + (long long)seg * I.N;
+    if (cnt == 0) return TOPOT_OK;
+    TOPOT_CUDA(cudaMemcpy(h_idx, t->arena_idx + base, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
+    if (t->dtype == TOPOT_U8) {
+        std::vector<int16_t> tmp((size_t)cnt);
+        TOPOT_CUDA(cudaMemcpy(tmp.data(), reinterpret_cast<int16_t*>(t->arena_val) + base, sizeof(int16_t) * cnt,
+                              cudaMemcpyDeviceToHost));
+        for (long long i = 0; i < cnt; ++i) h_val[i] = tmp[(size_t)i];
+    } else {
+        TOPOT_CUDA(cudaMemcpy(h_val, reinterpret_cast<int32_t*>(t->arena_val) + base, sizeof(int32_t) * cnt,
+                              cudaMemcpyDeviceToHost));
+    }
+    return TOPOT_OK;
+}
+
+topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
+    if (!t) return fail(TOPOT_ERR_INVALID_ARG, "tables_set_tuning: NULL handle");
+    if (!tuning) {
+        t->tuning = topot_tuning{};
+        return TOPOT_OK;
+    }
+    const topot_tuning& u = *tuning;
+    if ((u.ect_dirs_per_warp && u.ect_dirs_per_warp != 8 && u.ect_dirs_per_warp != 16 && u.ect_dirs_per_warp != 32) ||
+        (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4) ||
+        u.chunk < 0 || (u.chunk % 256) != 0 || u.ctas_per_sm < 0 || u.ctas_per_sm > 32)
+        return fail(TOPOT_ERR_INVALID_ARG, "tables_set_tuning: value out of range");
+    t->tuning = u;
+    return TOPOT_OK;
+}
+
+void free_tables(topot_tables* t) {
+    if (!t) return;
+    if (t->ws) cudaFree(t->ws);
+    if (t->arena_val) cudaFree(t->arena_val);
+    if (t->arena_idx) cudaFree(t->arena_idx);
+    if (t->meta) cudaFree(t->meta);
+    delete t;
+}
+
+// ---- grid transforms ---------------------------------------------------------------------------
+
+static topot_status grid_transform(const char* name, int mode, const topot_tables* tc, const double* d_dirs, int D,
+                                   int per_image_dirs, double t_min, double t_max, int T, int32_t* d_out,
+                                   void* stream) {
+    topot_tables* t = const_cast<topot_tables*>(tc);
+    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
+    if (T < 2 || !(t_max > t_min) || !std::isfinite(t_min) || !std::isfinite(t_max))
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": need T >= 2 and finite t_min < t_max");
+    if (t->host_valid) {
+        for (long long v : t->h_absum)
+            if (v >= (1ll << 31))
+                return fail(TOPOT_ERR_OVERFLOW, std::string(name) + ": sum |Delta^-| >= 2^31 overflows int32");
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nsets = per_image_dirs ? t->B : 1;
+    const int NO = t->NO;
+    const int td = hist_tile(t, D, D / NO, T);
+    if (hist_smem_bytes(td, T) > 200 * 1024)
+        return fail(TOPOT_ERR_UNSUPPORTED, std::string(name) + ": too many thresholds for the shared histogram");
+    const int npairs = t->B * NO * (mode == kModeRadon ? 2 : 1);
+    const size_t out_elems = (size_t)t->B * D * T;
+    const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
+                        sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * T +
+                        (mode == kModeRadon ? sizeof(int32_t) * out_elems : 0) + 8 * 256;
+    topot_status s = ensure_ws(t, need);
+    if (s != TOPOT_OK) return s;
+    Carver cv{reinterpret_cast<char*>(t->ws)};
+    EvalPlan P{};
+    P.mode = mode;
+    P.nsets = nsets;
+    P.D = D;
+    P.tile_dirs = td;
+    P.chunk_req = t->tuning.chunk;
+    P.target_items = t->sm_count * 16;
+    P.npairs = npairs;
+    P.max_items = 1ll << 40;
+    P.dirs = d_dirs;
+    P.ctl = cv.take<int>(4);
+    P.perm = cv.take<int>((size_t)nsets * D);
+    P.rank = cv.take<int>((size_t)nsets * D);
+    P.boff = cv.take<int>((size_t)nsets * (NO + 1));
+    P.pair_items = cv.take<long long>(npairs + 1);
+    P.pair_chunks = cv.take<int>(npairs);
+    P.thr = cv.take<double>(T);
+    P.T = T;
+    P.t_min = t_min;
+    P.t_max = t_max;
+    int32_t* hi = mode == kModeRadon ? cv.take<int32_t>(out_elems) : nullptr;
+
+    TOPOT_CUDA(cudaMemsetAsync(d_out, 0, sizeof(int32_t) * out_elems, st));
+    if (hi) TOPOT_CUDA(cudaMemsetAsync(hi, 0, sizeof(int32_t) * out_elems, st));
+    TOPOT_CUDA(launch_dir_prep(P, t->n, st));
+    TOPOT_CUDA(launch_plan(P, t->dev(), st));
+    int per_sm = std::max(1, (int)((220 * 1024) / (hist_smem_bytes(td, T) + 1024)));
+    per_sm = std::min(per_sm, 8);
+    if (t->tuning.ctas_per_sm > 0) per_sm = std::min(per_sm, t->tuning.ctas_per_sm);
+    TOPOT_CUDA(launch_hist(P, t->dev(), td, d_out, hi, t->sm_count * per_sm, st));
+    TOPOT_CUDA(launch_hist_finish(mode, t->B, D, T, t->chi, d_out, hi, st));
+    return TOPOT_OK;
+}
+
+topot_status ect(const topot_tables* t, const double* d_dirs, int D, int per_image_dirs, double t_min,
+                 double t_max, int T, int32_t* d_out, void* stream) {
+    return grid_transform("ect", kModeECT, t, d_dirs, D, per_image_dirs, t_min, t_max, T, d_out, stream);
+}
+
+topot_status radon(const topot_tables* t, const double* d_dirs, int D, int per_image_dirs, double t_min,
+                   double t_max, int T, int32_t* d_out, void* stream) {
+    return grid_transform("radon", kModeRadon, t, d_dirs, D, per_image_dirs, t_min, t_max, T, d_out, stream);
+}
+
+// ---- hybrid transforms ----------------------------------------------------------------------
+
+static topot_status ht_common(const char* name, const topot_tables* tc, topot_kernel kernel,
+                              topot_precision precision, const double* d_dirs, int D, int per_image_dirs,
+                              bool adjoint, const double* d_gout, double* d_out, void* stream) {
+    topot_tables* t = const_cast<topot_tables*>(tc);
+    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out || (adjoint && !d_gout))
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
+    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad kernel");
+    if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nsets = per_image_dirs ? t->B : 1;
+    const int NO = t->NO;
+    int dl = 1;
+    if (precision == TOPOT_FP32C) {
+        dl = t->tuning.ht_dirs_per_lane;
+        const int per_orthant = D / NO;
+        if (dl == 0) dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+        if (adjoint && dl > 2) dl = 2;
+    }
+    const int tdh = 32 * dl;
+    const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
+    const int ncomp = adjoint ? nk * t->n : nk;
+    const int npairs = t->B * NO;
+    const int target = t->sm_count * 16;
+    long long max_items;
+    if (t->tuning.chunk > 0) {
+        max_items = 0;
+        for (int b = 0; b < t->B; ++b)
+            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.chunk - 1) / t->tuning.chunk);
+    } else {
+        max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
+    }
+    const size_t part_elems = (size_t)max_items * tdh * ncomp;
+    const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
+                        sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * part_elems +
+                        8 * 256;
+    topot_status s = ensure_ws(t, need);
+    if (s != TOPOT_OK) return s;
+    Carver cv{reinterpret_cast<char*>(t->ws)};
+    EvalPlan P{};
+    P.mode = kModeHT;
+    P.nsets = nsets;
+    P.D = D;
+    P.tile_dirs = tdh;
+    P.chunk_req = t->tuning.chunk;
+    P.target_items = target;
+    P.npairs = npairs;
+    P.max_items = max_items;
+    P.dirs = d_dirs;
+    P.ctl = cv.take<int>(4);
+    P.perm = cv.take<int>((size_t)nsets * D);
+    P.rank = cv.take<int>((size_t)nsets * D);
+    P.boff = cv.take<int>((size_t)nsets * (NO + 1));
+    P.pair_items = cv.take<long long>(npairs + 1);
+    P.pair_chunks = cv.take<int>(npairs);
+    P.thr = nullptr;
+    P.T = 0;
+    double* part = cv.take<double>(part_elems);
+
+    TOPOT_CUDA(launch_dir_prep(P, t->n, st));
+    TOPOT_CUDA(launch_plan(P, t->dev(), st));
+    const int per_sm = t->tuning.ctas_per_sm > 0 ? t->tuning.ctas_per_sm : 4;
+    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, adjoint, dl, t->sm_count * per_sm, part, st));
+    if (adjoint)
+        TOPOT_CUDA(launch_ht_adj_combine(P, t->n, t->B, kernel, precision, tdh, part, d_gout, d_out, st));
+    else
+        TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, d_out, st));
+    return TOPOT_OK;
+}
+
+topot_status hybrid_transform(const topot_tables* t, topot_kernel kernel, topot_precision precision,
+                              const double* d_dirs, int D, int per_image_dirs, double* d_out, void* stream) {
+    return ht_common("hybrid_transform", t, kernel, precision, d_dirs, D, per_image_dirs, false, nullptr, d_out,
+                     stream);
+}
+
+topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel, topot_precision precision,
+                                   const double* d_dirs, int D, int per_image_dirs, const double* d_gout,
+                                   double* d_gdirs, void* stream) {
+    return ht_common("hybrid_transform_grad", t, kernel, precision, d_dirs, D, per_image_dirs, true, d_gout,
+                     d_gdirs, stream);
+}
+
+}  // extern "C"

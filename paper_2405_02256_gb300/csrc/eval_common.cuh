@@ -1,0 +1,89 @@
+// Work planning shared by the evaluation kernels (ECT, Radon, hybrid transform and
+// its adjoint).
+//
+// A "pair" is (image b, orthant o) -- for the Radon transform (b, o, part) with part 0
+// the sublevel histogram on table o and part 1 the superlevel histogram on table
+// o ^ (2^n - 1).  The directions of a pair are the directions of b's direction set
+// whose sign vector is o (grouped by dir_prep).  A work item is (pair, tile of
+// directions, chunk of the pair's critical table); items are numbered pair by pair,
+// tile-major, so that partial results of one direction are laid out in chunk order.
+#pragma once
+
+#include "internal.cuh"
+
+namespace topot {
+
+enum EvalMode : int { kModeECT = 0, kModeRadon = 1, kModeHT = 2 };
+
+struct EvalPlan {
+    int mode;
+    int nsets;                 // 1 (shared directions) or B
+    int D;                     // directions per set
+    int tile_dirs;             // directions per work item
+    int chunk_req;             // requested critical points per item (0 = automatic)
+    int target_items;          // automatic chunking aims at about this many items
+    int npairs;
+    long long max_items;       // capacity of the per-item partial buffers
+    const double* dirs;        // [nsets][D][n]
+    int* perm;                 // [nsets][D]: direction ids grouped by orthant
+    int* rank;                 // [nsets][D]: position of each direction in its group
+    int* boff;                 // [nsets][NO + 1]: group offsets
+    long long* pair_items;     // [npairs + 1]: exclusive prefix of items
+    int* pair_chunks;          // [npairs]
+    int* ctl;                  // [0] item counter, [1] chunk, [2] number of items
+    double* thr;               // [T] thresholds (ECT / Radon)
+    int T;
+    double t_min, t_max;
+};
+
+__device__ __forceinline__ int orthant_of(const double* xi, int n) {
+    int o = 0;
+    for (int k = 0; k < n; ++k)
+        if (xi[k] < 0.0) o |= 1 << k;   // zero (and -0.0) -> eps_k = +1
+    return o;
+}
+
+// Pair -> (image, orthant, part).
+__device__ __forceinline__ void decode_pair(int mode, int NO, int p, int& b, int& o, int& part) {
+    if (mode == kModeRadon) {
+        part = p & 1;
+        p >>= 1;
+    } else {
+        part = 0;
+    }
+    b = p / NO;
+    o = p - b * NO;
+}
+
+// Segment (table) used by a pair, and the sign applied to its values.
+__device__ __forceinline__ int pair_segment(int mode, int NO, int o, int part, int& sign) {
+    sign = 1;
+    if (mode == kModeECT) return o;
+    if (mode == kModeRadon) return part ? (o ^ (NO - 1)) : o;
+    // hybrid: representative orthants have bit n-1 clear; the partner's table is -Delta
+    if (o & (NO >> 1)) {
+        sign = -1;
+        return NO + (o ^ (NO - 1));
+    }
+    return NO + o;
+}
+
+// Item -> (pair, tile, chunk) by binary search over the item prefix.
+__device__ __forceinline__ void decode_item(const EvalPlan& P, long long item, int& pair, int& tile,
+                                            int& chunk) {
+    int lo = 0, hi = P.npairs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.pair_items[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    pair = lo;
+    const long long local = item - P.pair_items[lo];
+    const int nch = P.pair_chunks[lo];
+    tile = (int)(local / nch);
+    chunk = (int)(local - (long long)tile * nch);
+}
+
+cudaError_t launch_dir_prep(const EvalPlan& P, int n, cudaStream_t st);
+cudaError_t launch_plan(const EvalPlan& P, const TablesDev& t, cudaStream_t st);
+
+}  // namespace topot

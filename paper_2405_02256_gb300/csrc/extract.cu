@@ -1,0 +1,349 @@
+// K1: critical-table extraction (Section 3, Delta^-; Section 4.2, preprocessing).
+//
+// One block per tile.  A tile is a run of vertices that is contiguous in linear
+// vertex order: R full rows of one plane (m_0 <= W) or one W-wide piece of a row.
+// The block
+//   1. stages the tile's pixels plus a one-vertex halo (three planes in 3-D) in
+//      shared memory -- 1-D bulk copies (TMA, cp.async.bulk) for 16-byte aligned row
+//      interiors, plain loads for the halo and unaligned rows; pixels outside the
+//      image get a sentinel so that a box that leaves the image contributes nothing;
+//   2. evaluates, for every vertex and every orthant o, the lower-star value
+//      Delta^-_o(v) = sum_{delta in {0,1}^n} (-1)^|delta| min(phi over box(v, v - delta (.) eps_o))
+//      from the 3^n neighbourhood (all 2^n orthants share the edge / face minima);
+//   3. compacts the non-zero values of the 2^n lower tables and of the 2^(n-1)
+//      Delta = Delta^-_r - Delta^-_{-r} tables in vertex order: warp ballots, a block
+//      scan of the per-warp counts and a decoupled look-back over the tiles of the
+//      same image (tiles are numbered by an atomic ticket, so every predecessor
+//      belongs to a block that has already started);
+//   4. adds chi = sum Delta^-_0 and sum |Delta^-_o| of the tile to per-image totals.
+#include "internal.cuh"
+
+namespace topot {
+
+constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate available
+constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix available
+constexpr unsigned long long kCountMask = (1ull << 62) - 1;
+
+template <typename Tin> struct PixTraits;
+template <> struct PixTraits<uint8_t> {
+    // u8 values are >= 0: a zero sentinel makes the minimum over any box that leaves
+    // the image 0, i.e. that box contributes nothing.
+    static constexpr bool kSigned = false;
+    __device__ static int sentinel() { return 0; }
+    __device__ static int fix(int v) { return v; }
+};
+template <> struct PixTraits<int32_t> {
+    static constexpr bool kSigned = true;
+    __device__ static int sentinel() { return INT32_MIN; }
+    __device__ static int fix(int v) { return v == INT32_MIN ? 0 : v; }
+};
+
+// Lower-star values of one vertex for all 2^NDIM orthants.  `c` points at the vertex
+// in the staged buffer; rs = row stride, ps = plane stride (elements).
+template <int NDIM, typename Tin>
+__device__ __forceinline__ void lower_star(const Tin* c, int rs, int ps, int (&out)[1 << NDIM]) {
+    using PT = PixTraits<Tin>;
+    auto nb = [&](int dx, int dy, int dz) -> int { return (int)c[dz * ps + dy * rs + dx]; };
+    const int a = nb(0, 0, 0);
+    if constexpr (NDIM == 2) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int d0 = (o & 1) ? 1 : -1;
+            const int d1 = (o & 2) ? 1 : -1;
+            const int e0 = min(a, nb(d0, 0, 0));
+            const int e1 = min(a, nb(0, d1, 0));
+            const int sq = min(min(e0, e1), nb(d0, d1, 0));
+            out[o] = PT::fix(a) - PT::fix(e0) - PT::fix(e1) + PT::fix(sq);
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int d0 = (o & 1) ? 1 : -1;
+            const int d1 = (o & 2) ? 1 : -1;
+            const int d2 = (o & 4) ? 1 : -1;
+            const int e0 = min(a, nb(d0, 0, 0));
+            const int e1 = min(a, nb(0, d1, 0));
+            const int e2 = min(a, nb(0, 0, d2));
+            const int f01 = min(min(e0, e1), nb(d0, d1, 0));
+            const int f02 = min(min(e0, e2), nb(d0, 0, d2));
+            const int f12 = min(min(e1, e2), nb(0, d1, d2));
+            const int cu = min(min(f01, f02), min(f12, nb(d0, d1, d2)));
+            out[o] = PT::fix(a) - PT::fix(e0) - PT::fix(e1) - PT::fix(e2) + PT::fix(f01) +
+                     PT::fix(f02) + PT::fix(f12) - PT::fix(cu);
+        }
+    }
+}
+
+template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
+__global__ void __launch_bounds__(BLOCK) k_extract(ExtractArgs p) {
+    using PT = PixTraits<Tin>;
+    constexpr int NO = 1 << NDIM;              // orthants
+    constexpr int S = NO + NO / 2;             // segments
+    constexpr int NW = BLOCK / 32;
+    constexpr int PAD = 16 / (int)sizeof(Tin); // interior starts 16 bytes into a row
+    constexpr int NP = (NDIM == 3) ? 3 : 1;    // staged planes
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    int* sh_int = reinterpret_cast<int*>(smem_raw + 16);               // [8]
+    long long* sh_pref = reinterpret_cast<long long*>(smem_raw + 48);  // [S]
+    long long* sh_acc = sh_pref + S;                                   // [1 + NO]
+    int* sh_cnt = reinterpret_cast<int*>(sh_acc + 1 + NO);             // [S][K][NW]
+    size_t stage_off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * K * NW;
+    stage_off = (stage_off + 15) & ~size_t(15);
+    Tin* stage = reinterpret_cast<Tin*>(smem_raw + stage_off);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const TablesDev& T = p.t;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        const unsigned ticket = atomicAdd(p.ticket, 1u);
+        // image owning this tile: last b with tile_begin <= ticket
+        int lo = 0, hi = T.B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (T.img[mid].tile_begin <= (long long)ticket) lo = mid; else hi = mid - 1;
+        }
+        sh_int[0] = (int)ticket;
+        sh_int[1] = lo;
+    }
+    if (tid < 1 + NO) sh_acc[tid] = 0;
+    __syncthreads();
+
+    const long long ticket = sh_int[0];
+    const int b = sh_int[1];
+    const ImgDesc& I = T.img[b];
+    const int m0 = I.m[0], m1 = I.m[1], m2 = I.m[2];
+    const long long lt = ticket - I.tile_begin;
+    const long long ntiles_img = (long long)I.tiles_per_plane * m2;
+    const int z = (int)(lt / I.tiles_per_plane);
+    const int rem = (int)(lt - (long long)z * I.tiles_per_plane);
+    const int rb = rem / I.segs_per_row;
+    const int sg = rem - rb * I.segs_per_row;
+    const int y0 = rb * I.R;
+    const int x0 = sg * I.W;
+    const int rows = min(I.R, m1 - y0);
+    const int cols = min(I.W, m0 - x0);
+    const int nverts = rows * cols;
+    const long long L0 = ((long long)z * m1 + y0) * m0 + x0;
+
+    // ---- 1. stage pixels + halo -------------------------------------------------------
+    const Tin* img = reinterpret_cast<const Tin*>(p.pixels) + I.offset;
+    const int RS = p.row_stride;
+    const int PS = p.stage_rows * RS;
+    const int srows = rows + 2;
+    const bool tma_cols = ((cols * (int)sizeof(Tin)) & 15) == 0;
+    unsigned tma_bytes = 0;
+    for (int q = tid; q < NP * srows; q += BLOCK) {
+        const int pl = q / srows, rr = q - pl * srows;
+        const int zz = (NDIM == 3) ? z + pl - 1 : z;
+        const int yy = y0 + rr - 1;
+        Tin* dst = stage + pl * PS + rr * RS;
+        const bool inside = zz >= 0 && zz < m2 && yy >= 0 && yy < m1;
+        if (!inside) continue;
+        const Tin* src = img + ((long long)zz * m1 + yy) * m0 + x0;
+        dst[PAD - 1] = x0 > 0 ? src[-1] : (Tin)PT::sentinel();
+        dst[PAD + cols] = (x0 + cols < m0) ? src[cols] : (Tin)PT::sentinel();
+    }
+    // rows outside the image, and rows whose interior is not 16-byte aligned
+    for (int q = 0; q < NP * srows; ++q) {
+        const int pl = q / srows, rr = q - pl * srows;
+        const int zz = (NDIM == 3) ? z + pl - 1 : z;
+        const int yy = y0 + rr - 1;
+        Tin* dst = stage + pl * PS + rr * RS;
+        const bool inside = zz >= 0 && zz < m2 && yy >= 0 && yy < m1;
+        if (!inside) {
+            for (int c = tid - 1; c <= cols; c += BLOCK) dst[PAD + c] = (Tin)PT::sentinel();
+            continue;
+        }
+        const Tin* src = img + ((long long)zz * m1 + yy) * m0 + x0;
+        const bool aligned = tma_cols && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
+        if (aligned) {
+            tma_bytes += (unsigned)(cols * sizeof(Tin));
+        } else {
+            for (int c = tid; c < cols; c += BLOCK) dst[PAD + c] = src[c];
+        }
+    }
+    __syncthreads();   // mbarrier initialised; generic-proxy halo writes done
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar, tma_bytes);
+        if (tma_bytes) {
+            for (int q = 0; q < NP * srows; ++q) {
+                const int pl = q / srows, rr = q - pl * srows;
+                const int zz = (NDIM == 3) ? z + pl - 1 : z;
+                const int yy = y0 + rr - 1;
+                if (!(zz >= 0 && zz < m2 && yy >= 0 && yy < m1)) continue;
+                const Tin* src = img + ((long long)zz * m1 + yy) * m0 + x0;
+                if (tma_cols && ((reinterpret_cast<uintptr_t>(src) & 15) == 0))
+                    bulk_g2s(stage + pl * PS + rr * RS + PAD, src, (unsigned)(cols * sizeof(Tin)), bar);
+            }
+        }
+    }
+    mbar_wait_bounded(bar, 0, T.err);
+    __syncthreads();
+
+    // ---- 2. lower-star values, kept in registers --------------------------------------
+    int vals[K][NO];
+    long long chi_acc = 0;
+    long long abs_acc[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) abs_acc[o] = 0;
+    bool bad_pixel = false;
+    const Tin* center0 = stage + (NP == 3 ? PS : 0) + RS + PAD;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = k * BLOCK + tid;
+        if (j < nverts) {
+            int r = 0, c = j;
+            if (rows > 1) { r = (int)fastdiv((uint32_t)j, I.div0); c = j - r * m0; }
+            const Tin* cp = center0 + r * RS + c;
+            lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
+            if constexpr (PT::kSigned) {
+                const int a = (int)cp[0];
+                bad_pixel |= (a >= (1 << 26)) || (a <= -(1 << 26));
+            }
+            chi_acc += vals[k][0];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) abs_acc[o] += abs(vals[k][o]);
+        } else {
+#pragma unroll
+            for (int o = 0; o < NO; ++o) vals[k][o] = 0;
+        }
+    }
+    if (bad_pixel) dev_set_error(T.err, kDevErrOverflow);
+
+    auto seg_value = [&](int k, int s) -> int {
+        return s < NO ? vals[k][s] : vals[k][s - NO] - vals[k][(s - NO) ^ (NO - 1)];
+    };
+
+    // ---- 3a. per-warp counts ------------------------------------------------------------
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const unsigned bal = __ballot_sync(0xffffffffu, seg_value(k, s) != 0);
+            if (lane == 0) sh_cnt[(s * K + k) * NW + warp] = __popc(bal);
+        }
+    }
+    // chi and sum |Delta^-| of the tile
+    chi_acc = warp_sum(chi_acc);
+#pragma unroll
+    for (int o = 0; o < NO; ++o) abs_acc[o] = warp_sum(abs_acc[o]);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[0]), (unsigned long long)chi_acc);
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[1 + o]), (unsigned long long)abs_acc[o]);
+    }
+    __syncthreads();
+
+    // ---- 3b. block scan per segment + decoupled look-back --------------------------------
+    if (tid < S) {
+        const int s = tid;
+        int run = 0;
+        int* cs = sh_cnt + s * K * NW;
+        for (int q = 0; q < K * NW; ++q) {
+            const int c = cs[q];
+            cs[q] = run;
+            run += c;
+        }
+        const unsigned long long agg = (unsigned long long)run;
+        unsigned long long* st = p.status + ticket * S + s;
+        long long prefix = 0;
+        if (lt == 0) {
+            st_relaxed_u64(st, kFlagP | agg);
+        } else {
+            st_relaxed_u64(st, kFlagA | agg);
+            long long q = ticket - 1;
+            const unsigned long long t0 = dev_time_ns();
+            bool timed_out = false;
+            while (true) {
+                const unsigned long long w = ld_relaxed_u64(p.status + q * S + s);
+                const unsigned long long flag = w & ~kCountMask;
+                if (flag == 0) {
+                    if (dev_time_ns() - t0 > kWaitLimitNs) { timed_out = true; break; }
+                    continue;
+                }
+                prefix += (long long)(w & kCountMask);
+                if (flag == kFlagP) break;
+                --q;
+            }
+            if (timed_out) {
+                dev_set_error(T.err, kDevErrTimeout);
+                prefix = 0;
+            }
+            st_relaxed_u64(st, kFlagP | ((unsigned long long)prefix + agg));
+        }
+        sh_pref[s] = prefix;
+        if (lt == ntiles_img - 1) T.seg_count[(long long)b * S + s] = prefix + (long long)agg;
+    }
+    if (tid == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&T.chi[b]), (unsigned long long)sh_acc[0]);
+        for (int o = 0; o < NO; ++o)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&T.absum[(long long)b * NO + o]),
+                      (unsigned long long)sh_acc[1 + o]);
+    }
+    __syncthreads();
+
+    // ---- 3c. scatter the compacted entries --------------------------------------------
+    Tval* aval = reinterpret_cast<Tval*>(T.arena_val);
+    const unsigned lt_mask = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = k * BLOCK + tid;
+        int r = 0, c = j;
+        if (rows > 1) { r = (int)fastdiv((uint32_t)(j < nverts ? j : 0), I.div0); c = j - r * m0; }
+        const int vidx = (int)(L0 + (long long)r * m0 + c);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int v = seg_value(k, s);
+            const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
+            if (v != 0) {
+                const long long pos = I.seg_base + (long long)s * I.N + sh_pref[s] +
+                                      sh_cnt[(s * K + k) * NW + warp] + __popc(bal & lt_mask);
+                T.arena_idx[pos] = vidx;
+                aval[pos] = (Tval)v;
+            }
+        }
+    }
+}
+
+// ---- host-side launch ----------------------------------------------------------------------
+
+template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
+static cudaError_t launch_extract_t(const ExtractArgs& a, size_t smem, cudaStream_t st) {
+    auto kern = k_extract<NDIM, Tin, Tval, BLOCK, K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)a.num_tiles, BLOCK, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tile geometry shared with the host code: vertices per tile and block size.
+int extract_block(int n) { return n == 2 ? 512 : 512; }
+int extract_k(int n) { return n == 2 ? 8 : 4; }
+
+size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows) {
+    const int NO = 1 << n, S = NO + NO / 2;
+    const int NW = extract_block(n) / 32;
+    size_t off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * extract_k(n) * NW;
+    off = (off + 15) & ~size_t(15);
+    const int NP = n == 3 ? 3 : 1;
+    return off + (size_t)NP * stage_rows * row_stride * elem_bytes;
+}
+
+cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st) {
+    const size_t smem = extract_smem_bytes(n, dtype == TOPOT_U8 ? 1 : 4, a.row_stride, a.stage_rows);
+    if (n == 2) {
+        if (dtype == TOPOT_U8) return launch_extract_t<2, uint8_t, int16_t, 512, 8>(a, smem, st);
+        return launch_extract_t<2, int32_t, int32_t, 512, 8>(a, smem, st);
+    }
+    if (dtype == TOPOT_U8) return launch_extract_t<3, uint8_t, int16_t, 512, 4>(a, smem, st);
+    return launch_extract_t<3, int32_t, int32_t, 512, 4>(a, smem, st);
+}
+
+}  // namespace topot

@@ -1,0 +1,645 @@
+// K4 / K5 / K6 / K8: hybrid transforms and their adjoint.
+//
+// HT(xi) = sum_v Delta_eps(v) kbar(<xi, v>)          (closed form and sign of Lemma 3.1)
+// dHT/dxi_k = sum_v Delta_eps(v) kappa(<xi, v>) x_k(v), kappa = kbar'
+//
+// Work split: persistent grid over the plan's items (pair, tile of 32 * DL
+// directions, chunk of the Delta table).  The chunk is staged in shared memory as
+// lattice coordinates; every lane owns DL directions and all lanes of a warp read
+// the same critical point (shared-memory broadcast), so the kernel evaluations run
+// on the FMA and MUFU pipes with no divergence.  Warps take disjoint slices of the
+// chunk.
+//
+// Precision (FP32C): every term is formed in FP32 and added with Kahan compensation
+// per lane; at the end of an item the eight warps' (sum - compensation) are added in
+// FP64 in warp order and stored as the item's partial; k_ht_combine adds the chunk
+// partials of each direction in chunk order in FP64.  The result is deterministic.
+// Laplace uses e^s = e^M e^{s - M} with M = sum_k |xi_k| / 2 = max_v s_v:
+// s - M = sum_k (|xi_k| / (m_k - 1)) q_k with integer q_k <= 0, so every FP32 exponent
+// is <= 0 (no overflow) and is a sum of non-positive terms (no cancellation).
+// FP64: the canonical FP64 dot product and library FP64 kernels, plain FP64 sums.
+#include "eval_common.cuh"
+
+namespace topot {
+
+constexpr int kHtBlock = 256;
+constexpr int kHtWarps = kHtBlock / 32;
+constexpr int kHtSub = 1024;        // staged critical points per round
+
+struct alignas(32) Dbl4 {
+    double x, y, z, w;
+};
+
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float term) {
+    const float y = __fsub_rn(term, c);
+    const float t = __fadd_rn(sum, y);
+    c = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
+// J0 for |x| <= 2 from its ascending series (Abramowitz & Stegun 9.1.10):
+// J0(x) = sum_k (-y)^k / (k!)^2, y = x^2 / 4 <= 1; truncation after k = 9 < 1e-13.
+__device__ __forceinline__ float j0_series_f(float x) {
+    const float y = 0.25f * x * x;
+    float p = 1.0f / 13168189440000.0f;          // k = 9: 1 / (9!)^2
+    p = fmaf(p, -y, 1.0f / 1625702400.0f);        // k = 8
+    p = fmaf(p, -y, 1.0f / 25401600.0f);          // k = 7
+    p = fmaf(p, -y, 1.0f / 518400.0f);            // k = 6
+    p = fmaf(p, -y, 1.0f / 14400.0f);             // k = 5
+    p = fmaf(p, -y, 1.0f / 576.0f);               // k = 4
+    p = fmaf(p, -y, 1.0f / 36.0f);                // k = 3
+    p = fmaf(p, -y, 1.0f / 4.0f);                 // k = 2
+    p = fmaf(p, -y, 1.0f);                        // k = 1
+    return fmaf(p, -y, 1.0f);                     // k = 0
+}
+
+// J1 for |x| <= 2 (A&S 9.1.10): J1(x) = (x/2) sum_k (-y)^k / (k! (k+1)!).
+__device__ __forceinline__ float j1_series_f(float x) {
+    const float y = 0.25f * x * x;
+    float p = 1.0f / 131681894400.0f;             // k = 9: 1 / (9! 10!)
+    p = fmaf(p, -y, 1.0f / 14631321600.0f);       // k = 8
+    p = fmaf(p, -y, 1.0f / 203212800.0f);         // k = 7
+    p = fmaf(p, -y, 1.0f / 3628800.0f);           // k = 6
+    p = fmaf(p, -y, 1.0f / 86400.0f);             // k = 5
+    p = fmaf(p, -y, 1.0f / 2880.0f);              // k = 4
+    p = fmaf(p, -y, 1.0f / 144.0f);               // k = 3
+    p = fmaf(p, -y, 1.0f / 12.0f);                // k = 2
+    p = fmaf(p, -y, 1.0f / 2.0f);                 // k = 1
+    p = fmaf(p, -y, 1.0f);                        // k = 0
+    return 0.5f * x * p;
+}
+
+__device__ __forceinline__ float bessel_j0_f(float s) {
+    if (fabsf(s) <= 2.0f) return j0_series_f(s);
+    return (float)j0((double)s);
+}
+
+__device__ __forceinline__ float bessel_j1_f(float s) {
+    if (fabsf(s) <= 2.0f) return j1_series_f(s);
+    return (float)j1((double)s);
+}
+
+// sin and cos on the MUFU pipe for |s| <= pi (absolute error < 2^-21), accurate
+// library routine beyond.
+__device__ __forceinline__ void sincos_f(float s, float& sn, float& cs) {
+    if (fabsf(s) <= 3.14159f) {
+        sn = __sinf(s);
+        cs = __cosf(s);
+    } else {
+        sincosf(s, &sn, &cs);
+    }
+}
+
+// Per-lane direction coefficients.
+struct HtDir {
+    float w[3];      // LAPLACE: |xi_k| / (m_k - 1) * log2 e; others: xi_k / (2 (m_k - 1))
+    double xi[3];
+    bool valid;
+    int d;
+};
+
+// Shared prologue of the forward and adjoint kernels: item decode and staging.
+struct HtItem {
+    int b, o, sign, seg;
+    long long base, e_begin, e_end;
+    const ImgDesc* I;
+    int set, nd;
+};
+
+__device__ __forceinline__ HtItem ht_item(const EvalPlan& P, const TablesDev& t, long long item, int NO,
+                                          int tile_dirs, int& tile) {
+    HtItem it;
+    int pair, ch, part;
+    decode_item(P, item, pair, tile, ch);
+    decode_pair(P.mode, NO, pair, it.b, it.o, part);
+    it.seg = pair_segment(P.mode, NO, it.o, part, it.sign);
+    it.I = &t.img[it.b];
+    it.set = P.nsets == 1 ? 0 : it.b;
+    const int* bo = P.boff + (long long)it.set * (NO + 1);
+    it.nd = bo[it.o + 1] - bo[it.o];
+    const long long N = t.seg_count[(long long)it.b * t.S + it.seg];
+    it.base = it.I->seg_base + (long long)it.seg * it.I->N;
+    it.e_begin = (long long)ch * P.ctl[1];
+    it.e_end = min(N, it.e_begin + P.ctl[1]);
+    (void)tile_dirs;
+    return it;
+}
+
+// Stage critical points [e0, e0 + cnt) as lattice data: A = (p0, p1, p2, value) with
+// p = q (LAPLACE: q_k = i_k - (m_k - 1) if eps_k = +1 else -i_k) or c_k = 2 i_k - (m_k - 1);
+// X = (x0, x1, x2) embedding coordinates (adjoint only).
+template <int NDIM, int KERNEL, bool WITH_X, typename Tval>
+__device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, long long e0, int cnt,
+                                         float4* A, float4* X) {
+    const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
+    const ImgDesc& I = *it.I;
+    for (int i = threadIdx.x; i < cnt; i += kHtBlock) {
+        const uint32_t idx = (uint32_t)t.arena_idx[it.base + e0 + i];
+        const float v = (float)aval[it.base + e0 + i];
+        const uint32_t q1 = fastdiv(idx, I.div0);
+        int ii[3];
+        ii[0] = (int)(idx - q1 * (uint32_t)I.m[0]);
+        ii[1] = (int)q1;
+        ii[2] = 0;
+        if (NDIM == 3) {
+            const uint32_t q2 = fastdiv(q1, I.div1);
+            ii[1] = (int)(q1 - q2 * (uint32_t)I.m[1]);
+            ii[2] = (int)q2;
+        }
+        float p[3], c[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c[k] = (float)(2 * ii[k] - (I.m[k] - 1));
+            if (KERNEL == TOPOT_LAPLACE)
+                p[k] = ((it.o >> k) & 1) ? (float)(-ii[k]) : (float)(ii[k] - (I.m[k] - 1));
+            else
+                p[k] = c[k];
+        }
+        if (NDIM == 2) p[2] = 0.0f;
+        A[i] = make_float4(p[0], p[1], p[2], v);
+        if (WITH_X) {
+            float x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) x[k] = (k < NDIM) ? c[k] / (float)(2 * (I.m[k] - 1)) : 0.0f;
+            X[i] = make_float4(x[0], x[1], x[2], 0.0f);
+        }
+    }
+}
+
+template <int NDIM, int KERNEL>
+__device__ __forceinline__ void ht_dir(const EvalPlan& P, const HtItem& it, int r, HtDir& hd) {
+    const int NO = 1 << NDIM;
+    hd.valid = r < it.nd;
+    hd.d = hd.valid ? P.perm[(long long)it.set * P.D + P.boff[(long long)it.set * (NO + 1) + it.o] + r] : 0;
+    const double* xp = P.dirs + ((long long)it.set * P.D + hd.d) * NDIM;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        hd.xi[k] = k < NDIM ? xp[k] : 0.0;
+        const double mk = (double)(it.I->m[k] - 1);
+        if (k >= NDIM) hd.w[k] = 0.0f;
+        else if (KERNEL == TOPOT_LAPLACE) hd.w[k] = (float)(fabs(hd.xi[k]) / mk * 1.4426950408889634);
+        else hd.w[k] = (float)(hd.xi[k] / (2.0 * mk));
+    }
+}
+
+// ---- forward, FP32 compensated ------------------------------------------------------------
+
+template <int NDIM, int KERNEL, int DL, typename Tval>
+__global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, double* part) {
+    constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
+    constexpr int TDH = 32 * DL;
+    constexpr int NO = 1 << NDIM;
+    __shared__ float4 A[kHtSub];
+    __shared__ double red[kHtWarps][TDH * NC];
+    __shared__ long long sh_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nitems = P.ctl[2];
+
+    while (true) {
+        __syncthreads();
+        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= nitems) break;
+        int tile;
+        const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        HtDir hd[DL];
+#pragma unroll
+        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+        float acc[DL][NC], cmp[DL][NC];
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
+
+        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
+            const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
+            __syncthreads();
+            ht_stage<NDIM, KERNEL, false, Tval>(t, it, e0, cnt, A, nullptr);
+            __syncthreads();
+            const int per = (cnt + kHtWarps - 1) / kHtWarps;
+            const int ws = warp * per, we = min(cnt, ws + per);
+            for (int e = ws; e < we; ++e) {
+                const float4 q = A[e];
+#pragma unroll
+                for (int j = 0; j < DL; ++j) {
+                    float z = q.x * hd[j].w[0];
+                    z = fmaf(q.y, hd[j].w[1], z);
+                    if (NDIM == 3) z = fmaf(q.z, hd[j].w[2], z);
+                    if (KERNEL == TOPOT_LAPLACE) {
+                        kahan_add(acc[j][0], cmp[j][0], q.w * exp2f(z));
+                    } else if (KERNEL == TOPOT_FOURIER) {
+                        float sn, cs;
+                        sincos_f(z, sn, cs);
+                        kahan_add(acc[j][0], cmp[j][0], q.w * sn);
+                        kahan_add(acc[j][1], cmp[j][1], q.w * cs);
+                    } else {
+                        kahan_add(acc[j][0], cmp[j][0], q.w * bessel_j0_f(z));
+                    }
+                }
+            }
+        }
+        // fixed-order FP64 reduction over warps -> item partial
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] - (double)cmp[j][c];
+        __syncthreads();
+        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            part[item * (TDH * NC) + i] = s;
+        }
+    }
+}
+
+// ---- forward, plain FP64 ---------------------------------------------------------------------
+
+template <int NDIM, int KERNEL, typename Tval>
+__global__ void __launch_bounds__(kHtBlock) k_ht_f64(EvalPlan P, TablesDev t, double* part) {
+    constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
+    constexpr int TDH = 32;
+    constexpr int NO = 1 << NDIM;
+    __shared__ Dbl4 XA[kHtSub / 2];
+    __shared__ double red[kHtWarps][TDH * NC];
+    __shared__ long long sh_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nitems = P.ctl[2];
+    const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
+    constexpr int SUB = kHtSub / 2;
+
+    while (true) {
+        __syncthreads();
+        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= nitems) break;
+        int tile;
+        const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        HtDir hd;
+        ht_dir<NDIM, TOPOT_FOURIER>(P, it, tile * TDH + lane, hd);
+        double acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+        const ImgDesc& I = *it.I;
+        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+            const int cnt = (int)min((long long)SUB, it.e_end - e0);
+            __syncthreads();
+            for (int i = tid; i < cnt; i += kHtBlock) {
+                const uint32_t idx = (uint32_t)t.arena_idx[it.base + e0 + i];
+                const double v = (double)aval[it.base + e0 + i];
+                const uint32_t q1 = fastdiv(idx, I.div0);
+                int ii[3] = {(int)(idx - q1 * (uint32_t)I.m[0]), (int)q1, 0};
+                if (NDIM == 3) {
+                    const uint32_t q2 = fastdiv(q1, I.div1);
+                    ii[1] = (int)(q1 - q2 * (uint32_t)I.m[1]);
+                    ii[2] = (int)q2;
+                }
+                double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < NDIM; ++k)
+                    x[k] = __ddiv_rn((double)(2 * ii[k] - (I.m[k] - 1)), (double)(2 * (I.m[k] - 1)));
+                XA[i] = Dbl4{x[0], x[1], x[2], v};
+            }
+            __syncthreads();
+            const int per = (cnt + kHtWarps - 1) / kHtWarps;
+            const int ws = warp * per, we = min(cnt, ws + per);
+            for (int e = ws; e < we; ++e) {
+                const Dbl4 q = XA[e];
+                double s = __dmul_rn(hd.xi[0], q.x);
+                s = __dadd_rn(s, __dmul_rn(hd.xi[1], q.y));
+                if (NDIM == 3) s = __dadd_rn(s, __dmul_rn(hd.xi[2], q.z));
+                if (KERNEL == TOPOT_LAPLACE) {
+                    acc[0] += q.w * exp(s);
+                } else if (KERNEL == TOPOT_FOURIER) {
+                    double sn, cs;
+                    sincos(s, &sn, &cs);
+                    acc[0] += q.w * sn;
+                    acc[1] += q.w * cs;
+                } else {
+                    acc[0] += q.w * j0(s);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) red[warp][lane * NC + c] = acc[c];
+        __syncthreads();
+        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            part[item * (TDH * NC) + i] = s;
+        }
+    }
+}
+
+// ---- adjoint (FP32 compensated and FP64) ----------------------------------------------------
+// Partials per direction: LAPLACE / BESSEL: n sums  sum Delta kappa(s) x_k;
+// FOURIER: 2n sums  (sum Delta cos(s) x_k, sum Delta sin(s) x_k)  [d Re = +cos, d Im = -sin].
+
+template <int NDIM, int KERNEL, int DL, typename Tval>
+__global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t, double* part) {
+    constexpr int NK = KERNEL == TOPOT_FOURIER ? 2 : 1;
+    constexpr int NC = NK * NDIM;
+    constexpr int TDH = 32 * DL;
+    constexpr int NO = 1 << NDIM;
+    __shared__ float4 A[kHtSub / 2];
+    __shared__ float4 X[kHtSub / 2];
+    __shared__ double red[kHtWarps][TDH * NC];
+    __shared__ long long sh_item;
+    constexpr int SUB = kHtSub / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nitems = P.ctl[2];
+
+    while (true) {
+        __syncthreads();
+        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= nitems) break;
+        int tile;
+        const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        HtDir hd[DL];
+#pragma unroll
+        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+        float acc[DL][NC], cmp[DL][NC];
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
+
+        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+            const int cnt = (int)min((long long)SUB, it.e_end - e0);
+            __syncthreads();
+            ht_stage<NDIM, KERNEL, true, Tval>(t, it, e0, cnt, A, X);
+            __syncthreads();
+            const int per = (cnt + kHtWarps - 1) / kHtWarps;
+            const int ws = warp * per, we = min(cnt, ws + per);
+            for (int e = ws; e < we; ++e) {
+                const float4 q = A[e];
+                const float4 x = X[e];
+                const float xs[3] = {x.x, x.y, x.z};
+#pragma unroll
+                for (int j = 0; j < DL; ++j) {
+                    float z = q.x * hd[j].w[0];
+                    z = fmaf(q.y, hd[j].w[1], z);
+                    if (NDIM == 3) z = fmaf(q.z, hd[j].w[2], z);
+                    if (KERNEL == TOPOT_FOURIER) {
+                        float sn, cs;
+                        sincos_f(z, sn, cs);
+                        const float tc = q.w * cs, ts = q.w * sn;
+#pragma unroll
+                        for (int k = 0; k < NDIM; ++k) {
+                            kahan_add(acc[j][k], cmp[j][k], tc * xs[k]);
+                            kahan_add(acc[j][NDIM + k], cmp[j][NDIM + k], ts * xs[k]);
+                        }
+                    } else {
+                        const float kv = KERNEL == TOPOT_LAPLACE ? exp2f(z) : -bessel_j1_f(z);
+                        const float tk = q.w * kv;
+#pragma unroll
+                        for (int k = 0; k < NDIM; ++k) kahan_add(acc[j][k], cmp[j][k], tk * xs[k]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] - (double)cmp[j][c];
+        __syncthreads();
+        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            part[item * (TDH * NC) + i] = s;
+        }
+    }
+}
+
+template <int NDIM, int KERNEL, typename Tval>
+__global__ void __launch_bounds__(kHtBlock) k_ht_adj_f64(EvalPlan P, TablesDev t, double* part) {
+    constexpr int NK = KERNEL == TOPOT_FOURIER ? 2 : 1;
+    constexpr int NC = NK * NDIM;
+    constexpr int TDH = 32;
+    constexpr int NO = 1 << NDIM;
+    constexpr int SUB = kHtSub / 2;
+    __shared__ Dbl4 XA[SUB];
+    __shared__ double red[kHtWarps][TDH * NC];
+    __shared__ long long sh_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nitems = P.ctl[2];
+    const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
+
+    while (true) {
+        __syncthreads();
+        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= nitems) break;
+        int tile;
+        const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        HtDir hd;
+        ht_dir<NDIM, TOPOT_FOURIER>(P, it, tile * TDH + lane, hd);
+        double acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+        const ImgDesc& I = *it.I;
+        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+            const int cnt = (int)min((long long)SUB, it.e_end - e0);
+            __syncthreads();
+            for (int i = tid; i < cnt; i += kHtBlock) {
+                const uint32_t idx = (uint32_t)t.arena_idx[it.base + e0 + i];
+                const double v = (double)aval[it.base + e0 + i];
+                const uint32_t q1 = fastdiv(idx, I.div0);
+                int ii[3] = {(int)(idx - q1 * (uint32_t)I.m[0]), (int)q1, 0};
+                if (NDIM == 3) {
+                    const uint32_t q2 = fastdiv(q1, I.div1);
+                    ii[1] = (int)(q1 - q2 * (uint32_t)I.m[1]);
+                    ii[2] = (int)q2;
+                }
+                double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < NDIM; ++k)
+                    x[k] = __ddiv_rn((double)(2 * ii[k] - (I.m[k] - 1)), (double)(2 * (I.m[k] - 1)));
+                XA[i] = Dbl4{x[0], x[1], x[2], v};
+            }
+            __syncthreads();
+            const int per = (cnt + kHtWarps - 1) / kHtWarps;
+            const int ws = warp * per, we = min(cnt, ws + per);
+            for (int e = ws; e < we; ++e) {
+                const Dbl4 q = XA[e];
+                const double xs[3] = {q.x, q.y, q.z};
+                double s = __dmul_rn(hd.xi[0], q.x);
+                s = __dadd_rn(s, __dmul_rn(hd.xi[1], q.y));
+                if (NDIM == 3) s = __dadd_rn(s, __dmul_rn(hd.xi[2], q.z));
+                if (KERNEL == TOPOT_FOURIER) {
+                    double sn, cs;
+                    sincos(s, &sn, &cs);
+#pragma unroll
+                    for (int k = 0; k < NDIM; ++k) {
+                        acc[k] += q.w * cs * xs[k];
+                        acc[NDIM + k] += q.w * sn * xs[k];
+                    }
+                } else {
+                    const double kv = KERNEL == TOPOT_LAPLACE ? exp(s) : -j1(s);
+#pragma unroll
+                    for (int k = 0; k < NDIM; ++k) acc[k] += q.w * kv * xs[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) red[warp][lane * NC + c] = acc[c];
+        __syncthreads();
+        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            part[item * (TDH * NC) + i] = s;
+        }
+    }
+}
+
+// ---- combine (K6) ------------------------------------------------------------------------------
+
+// Sum of the chunk partials of direction d of image b, in chunk order.
+__device__ __forceinline__ void gather_partials(const EvalPlan& P, int NO, int tdh, int ncomp, int b, int d,
+                                                int o, const double* part, double* outc) {
+    const int set = P.nsets == 1 ? 0 : b;
+    const int r = P.rank[(long long)set * P.D + d];
+    const int pair = b * NO + o;
+    const int tile = r / tdh, dd = r - tile * tdh;
+    const long long nitems = P.pair_items[pair + 1] - P.pair_items[pair];
+    for (int c = 0; c < ncomp; ++c) outc[c] = 0.0;
+    if (nitems == 0) return;
+    const int nch = P.pair_chunks[pair];
+    const long long i0 = P.pair_items[pair] + (long long)tile * nch;
+    for (int ch = 0; ch < nch; ++ch) {
+        const double* pp = part + (i0 + ch) * (long long)(tdh * ncomp) + (long long)dd * ncomp;
+        for (int c = 0; c < ncomp; ++c) outc[c] += pp[c];
+    }
+}
+
+__global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision, int tdh,
+                             const double* part, double* out) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)B * P.D) return;
+    const int b = (int)(gid / P.D), d = (int)(gid - (long long)b * P.D);
+    const int NO = 1 << n;
+    const int set = P.nsets == 1 ? 0 : b;
+    const double* xi = P.dirs + ((long long)set * P.D + d) * n;
+    const int o = orthant_of(xi, n);
+    const int nc = kernel == TOPOT_FOURIER ? 2 : 1;
+    double v[2];
+    gather_partials(P, NO, tdh, nc, b, d, o, part, v);
+    const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
+    double scale = sign;
+    if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
+        double M = 0.0;
+        for (int k = 0; k < n; ++k) M += fabs(xi[k]);
+        scale *= exp(0.5 * M);
+    }
+    for (int c = 0; c < nc; ++c) out[gid * nc + c] = v[c] * scale;
+}
+
+// gdirs[set][d][k] = sum over images b of the set (all images when shared) of
+// sum_c gout[b][d][c] * dOut_c / dxi_k.
+__global__ void k_ht_adj_combine(EvalPlan P, int n, int B, int kernel, int precision, int tdh,
+                                 const double* part, const double* gout, double* gdirs) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)P.nsets * P.D) return;
+    const int set = (int)(gid / P.D), d = (int)(gid - (long long)set * P.D);
+    const int NO = 1 << n;
+    const double* xi = P.dirs + ((long long)set * P.D + d) * n;
+    const int o = orthant_of(xi, n);
+    const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
+    const int nc = nk * n;
+    const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
+    double scale = sign;
+    if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
+        double M = 0.0;
+        for (int k = 0; k < n; ++k) M += fabs(xi[k]);
+        scale *= exp(0.5 * M);
+    }
+    double g[3] = {0.0, 0.0, 0.0};
+    const int b0 = P.nsets == 1 ? 0 : set, b1 = P.nsets == 1 ? B : set + 1;
+    for (int b = b0; b < b1; ++b) {
+        double v[6];
+        gather_partials(P, NO, tdh, nc, b, d, o, part, v);
+        const double* go = gout + ((long long)b * P.D + d) * nk;
+        for (int k = 0; k < n; ++k) {
+            if (kernel == TOPOT_FOURIER)   // Re = sum D sin s: d/dxi = sum D cos s x; Im = sum D cos s: -sum D sin s x
+                g[k] += go[0] * v[k] - go[1] * v[n + k];
+            else
+                g[k] += go[0] * v[k];
+        }
+    }
+    for (int k = 0; k < n; ++k) gdirs[gid * n + k] = g[k] * scale;
+}
+
+// ---- launchers ---------------------------------------------------------------------------------
+
+template <int NDIM, int KERNEL, typename Tval>
+static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precision, bool adjoint, int dl,
+                               int grid, double* part, cudaStream_t st) {
+    if (precision == TOPOT_FP64) {
+        if (adjoint) k_ht_adj_f64<NDIM, KERNEL, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+        else k_ht_f64<NDIM, KERNEL, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+        return cudaGetLastError();
+    }
+    if (adjoint) {
+        switch (dl) {
+            case 1: k_ht_adj_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 2: k_ht_adj_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (dl) {
+            case 1: k_ht_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 2: k_ht_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 4: k_ht_f32<NDIM, KERNEL, 4, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int NDIM, typename Tval>
+static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint,
+                               int dl, int grid, double* part, cudaStream_t st) {
+    switch (kernel) {
+        case TOPOT_LAPLACE: return launch_ht_k<NDIM, TOPOT_LAPLACE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        case TOPOT_FOURIER: return launch_ht_k<NDIM, TOPOT_FOURIER, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        case TOPOT_BESSEL: return launch_ht_k<NDIM, TOPOT_BESSEL, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
+                      int grid, double* part, cudaStream_t st) {
+    if (t.n == 2) {
+        if (t.val_bytes == 2) return launch_ht_n<2, int16_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+        return launch_ht_n<2, int32_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+    }
+    if (t.val_bytes == 2) return launch_ht_n<3, int16_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+    return launch_ht_n<3, int32_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+}
+
+cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
+                              const double* part, double* out, cudaStream_t st) {
+    const long long rows = (long long)B * P.D;
+    k_ht_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
+                                  const double* part, const double* gout, double* gdirs, cudaStream_t st) {
+    const long long rows = (long long)P.nsets * P.D;
+    k_ht_adj_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part,
+                                                                       gout, gdirs);
+    return cudaGetLastError();
+}
+
+}  // namespace topot

@@ -1,0 +1,171 @@
+// Internal structures and device helpers of libtopot (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/topot.h"
+
+namespace topot {
+
+constexpr int kMaxDim = 3;
+
+// Device error word bits (OR-ed by kernels, read and cleared by tables_sync).
+enum DevErr : unsigned {
+    kDevErrOverflow = 1u,   // int32 pixel outside |phi| < 2^26, or |ECT| bound >= 2^31
+    kDevErrTimeout = 2u,    // a bounded wait gave up
+};
+
+// Time limit (ns of %globaltimer) of every device-side spin (look-back, mbarrier
+// waits).  A wait that runs out records kDevErrTimeout and returns instead of hanging.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long dev_time_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Unsigned division by a runtime constant d (1 <= d < 2^31) for dividends n < 2^31:
+// q = (n * mul) >> shift with mul = ceil(2^shift / d), shift = 31 + ceil(log2 d).
+struct FastDiv {
+    uint32_t d;
+    uint32_t mul;
+    uint32_t shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    f.shift = 31 + l;
+    unsigned __int128 num = (unsigned __int128)1 << f.shift;
+    f.mul = (uint32_t)((num + d - 1) / d);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv& f) {
+    return (uint32_t)(((unsigned long long)n * f.mul) >> f.shift);
+}
+
+// Per-image description, shared by extraction and evaluation kernels.
+struct ImgDesc {
+    long long offset;       // element offset of the image in the pixel buffer
+    long long N;            // vertices
+    long long seg_base;     // arena entry offset of segment 0 (segments are N apart)
+    long long tile_begin;   // first extraction tile (global numbering)
+    int m[kMaxDim];         // axis lengths, m_0 fastest; m_2 = 1 for n = 2
+    int W;                  // extraction tile width (columns)
+    int R;                  // extraction tile rows (1 when W < m_0)
+    int segs_per_row;       // ceil(m_0 / W)
+    int tiles_per_plane;    // ceil(m_1 / R) * segs_per_row
+    FastDiv div0;           // division by m_0
+    FastDiv div1;           // division by m_1
+};
+
+// Device view of a tables handle.
+struct TablesDev {
+    int n;                      // 2 or 3
+    int B;                      // images
+    int S;                      // segments per image: 2^n lower + 2^(n-1) delta
+    int val_bytes;              // 2 (int16, uint8 input) or 4 (int32 input)
+    const ImgDesc* img;         // [B]
+    int* arena_idx;             // [sum_b S * N_b]
+    void* arena_val;            // same length, int16 or int32
+    long long* seg_count;       // [B * S]
+    long long* chi;             // [B]
+    long long* absum;           // [B * 2^n]  sum_v |Delta^-_o(v)|
+    unsigned* err;              // device error word
+};
+
+// Arguments of the extraction kernel.
+struct ExtractArgs {
+    TablesDev t;
+    const void* pixels;
+    long long num_tiles;
+    unsigned* ticket;                 // zeroed before launch
+    unsigned long long* status;       // [num_tiles * S] look-back words, zeroed before launch
+    int row_stride;                   // staged row stride (elements, 16-byte multiple)
+    int stage_rows;                   // staged rows per plane (max R + 2)
+};
+
+__device__ __forceinline__ void dev_set_error(unsigned* err, unsigned bit) {
+    atomicOr(err, bit);
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---- mbarrier + bulk copy (TMA, non-tensor) helpers --------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Returns true when phase `parity` of the barrier has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 20000;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and the error bit set) if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = dev_time_ns();
+    while (dev_time_ns() - t0 < kWaitLimitNs) {
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+    dev_set_error(err, kDevErrTimeout);
+    return false;
+}
+
+// 1-D bulk copy global -> shared (cp.async.bulk), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// ---- warp helpers ---------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace topot
