@@ -1,0 +1,388 @@
+"""Benchmark of the hot path on synthetic images shaped like the paper's workloads.
+
+One step = one pass of the whole path over one batch: critical-table extraction of
+64 grayscale 2048 x 2048 images (Gaussian random field, correlation length 16,
+quantised to 0..255), ECT at 1024 directions x 512 thresholds, and the Laplace,
+Fourier and Bessel hybrid transforms at 4096 directions (|xi| log-uniform in
+[0.01, 1]) in FP32 with compensated sums.  The plain FP64 hybrid path is timed on a
+direction sample beside it.  Inputs (268 MB) and tables (~1.4 GB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+Prints one JSON line (see the design doc for every key).  ``--impl reference`` times the
+CPU oracle instead (a bounded sample of the same workload, same metric).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hybrid dir×crit-pt evals/s (FP32c vs FP64), ECT dirs/s, extraction GB/s"
+UNIT = "dir×crit-pt evals/s"
+WORKLOAD = "2D grayscale GRF, 64 x 2048x2048 uint8 (ell=16); ECT 1024 dirs x 512 thresholds; " \
+           "Laplace/Fourier/Bessel HT at 4096 dirs, |xi| log-uniform [0.01, 1]"
+B_IMAGES, SIDE, ELL = 64, 2048, 16.0
+D_ECT, T_ECT, D_HT = 1024, 512, 4096
+KERNELS = ("laplace", "fourier", "bessel")
+FP64_SAMPLE_DIRS = 128
+
+
+def make_images(count: int, side: int):
+    from paper_2405_02256_gb300 import synth
+    return [synth.grf((side, side), ELL, seed=1000 + b) for b in range(count)]
+
+
+def make_dirs():
+    from paper_2405_02256_gb300 import synth
+    return synth.circle_dirs(D_ECT), synth.random_2d_dirs(D_HT, 2, 0.01, 1.0)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_02256_gb300 import binding as tb
+    from paper_2405_02256_gb300 import synth
+
+    rank, world, local = _dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n_img = args.images
+
+    # ---- inputs (host, seeded), resident in HBM before the timed region ----------------
+    t0 = time.time()
+    imgs = make_images(n_img, args.side)
+    batch = tb.pack_images(imgs, device=dev)
+    host_pixels = batch.pixels.cpu().pin_memory()
+    dirs_ect_h, dirs_ht_h = make_dirs()
+    dirs_ect = torch.from_numpy(dirs_ect_h).to(dev)
+    dirs_ht = torch.from_numpy(dirs_ht_h).to(dev)
+    R = synth.image_radius(2)
+    setup_s = time.time() - t0
+
+    tabs = tb.tables_create(batch.shapes, batch.offsets)
+    tabs.build(batch.pixels)
+    tabs.sync()
+    n_delta = 0
+    n_lower = 0
+    for b in range(n_img):
+        for o in range(4):
+            nl, nd, _ = tabs.info(b, o)
+            n_lower += nl
+            n_delta += nd   # Delta table of o's representative: the table each direction of o uses
+    # evaluations per step: every direction of orthant o runs over |Delta_rep(o)| points
+    orth = np.array([sum(1 << k for k in range(2) if x[k] < 0) for x in dirs_ht_h])
+    terms = 0
+    for b in range(n_img):
+        for o in range(4):
+            terms += int(np.count_nonzero(orth == o)) * tabs.info(b, o)[1]
+    ect_updates = 0
+    orth_e = np.array([sum(1 << k for k in range(2) if x[k] < 0) for x in dirs_ect_h])
+    for b in range(n_img):
+        for o in range(4):
+            ect_updates += int(np.count_nonzero(orth_e == o)) * tabs.info(b, o)[0]
+    seg_entries = sum(tabs.info(b, o)[0] for b in range(n_img) for o in range(4)) + \
+        sum(tabs.info(b, r)[1] for b in range(n_img) for r in range(2))
+    ext_bytes = batch.pixels.numel() * 1 + seg_entries * 6      # u8 in, int32 idx + int16 value out
+
+    ect_out = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
+    ht_out = {k: torch.empty((n_img, D_HT, 2) if k == "fourier" else (n_img, D_HT), dtype=torch.float64, device=dev)
+              for k in KERNELS}
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        tabs.build(batch.pixels)
+        if ev is not None:
+            ev[1].record(stream)
+        tb.ect(tabs, dirs_ect, -R, R, T_ECT, out=ect_out)
+        if ev is not None:
+            ev[2].record(stream)
+        for i, k in enumerate(KERNELS):
+            tb.hybrid_transform(tabs, k, dirs_ht, "fp32c", out=ht_out[k])
+            if ev is not None:
+                ev[3 + i].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tabs.sync()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    ph = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(5)] for s in range(args.steps)])
+    ph_ms = ph.mean(axis=0)
+    value = terms * 3 * world / (ms_step / 1e3)
+
+    # ---- plain FP64 hybrid path on a direction sample ---------------------------------------
+    sample = dirs_ht[:FP64_SAMPLE_DIRS].contiguous()
+    sample_terms = 0
+    for b in range(n_img):
+        for o in range(4):
+            sample_terms += int(np.count_nonzero(orth[:FP64_SAMPLE_DIRS] == o)) * tabs.info(b, o)[1]
+    fp64 = {}
+    fp32_s = {}
+    for k in KERNELS:
+        for prec, store in (("fp64", fp64), ("fp32c", fp32_s)):
+            tb.hybrid_transform(tabs, k, sample, prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o64 = tb.hybrid_transform(tabs, k, sample, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            store[k] = {"ms": e0.elapsed_time(e1), "evals_per_s": sample_terms / (e0.elapsed_time(e1) / 1e3),
+                        "out": o64}
+    # accuracy of FP32C against the FP64 GPU path on the sample (relative to sum |Delta kbar| ~ |HT| bound)
+    acc = {}
+    for k in KERNELS:
+        a, b_ = fp32_s[k]["out"], fp64[k]["out"]
+        acc[k] = float(((a - b_).abs().max() / b_.abs().max().clamp_min(1e-300)).item())
+
+    # ---- end to end through the public API: host pixels in, results out -----------------------
+    ect_host = torch.empty(ect_out.shape, dtype=torch.int32).pin_memory()
+    ht_host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in ht_out.items()}
+    e2e_start, e2e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e2e_start.record(stream)
+    for _ in range(e2e_steps):
+        batch.pixels.copy_(host_pixels, non_blocking=True)
+        step()
+        ect_host.copy_(ect_out, non_blocking=True)
+        for k in KERNELS:
+            ht_host[k].copy_(ht_out[k], non_blocking=True)
+    e2e_stop.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2e_start.elapsed_time(e2e_stop) / e2e_steps
+    h2d = host_pixels.numel() * host_pixels.element_size()
+    d2h = ect_host.numel() * 4 + sum(v.numel() * 8 for v in ht_host.values())
+
+    clocks = clk.summary()
+    # dominant kernel of the step -> roofline
+    names = ["extract", "ect", "ht_laplace", "ht_fourier", "ht_bessel"]
+    dom = int(np.argmax(ph_ms))
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    # issue-slot peak of the FP32 / MUFU path: 4 schedulers x 32 lanes per SM per clock
+    lane_ops = sm_count * 128 * mhz * 1e6
+    # minimal instructions per term (FP32 pipe + MUFU), see the design doc
+    slots = {"ht_laplace": 7.0, "ht_fourier": 12.0, "ht_bessel": 17.0}
+    mufu = {"ht_laplace": 1.0, "ht_fourier": 2.0, "ht_bessel": 0.0}
+    if names[dom] == "extract":
+        achieved = ext_bytes / (ph_ms[dom] / 1e3) / 1e9
+        roof = {"kernel": "k_extract", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+    elif names[dom] == "ect":
+        per_upd = 12.0
+        achieved = ect_updates * per_upd / (ph_ms[dom] / 1e3) / 1e12
+        peak = lane_ops / 1e12
+        roof = {"kernel": "k_hist", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-ops/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "152 SM x 128 lanes x max clock"}
+    else:
+        nm = names[dom]
+        term_rate = terms / (ph_ms[dom] / 1e3)
+        peak_terms = min(lane_ops / slots[nm], (sm_count * 16 * mhz * 1e6 / mufu[nm]) if mufu[nm] else 1e30)
+        roof = {"kernel": "k_ht_f32<" + nm[3:] + ">", "bound": "alu", "achieved": term_rate / 1e9,
+                "peak": peak_terms / 1e9, "unit": "Gterms/s", "frac": term_rate / peak_terms, "traffic": None,
+                "peak_source": "issue slots (128 lanes/clk/SM) and MUFU (16/clk/SM) at max SM clock"}
+
+    launches_per_step = 1 + 4 + 4 * len(KERNELS)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8 tables / fp32c hybrid", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images": n_img, "side": args.side, "ect_dirs": D_ECT,
+                   "thresholds": T_ECT, "ht_dirs": D_HT, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "phases_ms": dict(zip(names, [float(x) for x in ph_ms])),
+        "ect_dirs_per_s": n_img * D_ECT * world / (ph_ms[1] / 1e3),
+        "ect_updates_per_s": ect_updates / (ph_ms[1] / 1e3),
+        "extraction_gbs": ext_bytes / (ph_ms[0] / 1e3) / 1e9,
+        "hybrid_fp32c_evals_per_s": {k: terms / (ph_ms[2 + i] / 1e3) for i, k in enumerate(KERNELS)},
+        "hybrid_fp64_evals_per_s": {k: fp64[k]["evals_per_s"] for k in KERNELS},
+        "fp32c_over_fp64_speedup": {k: fp32_s[k]["evals_per_s"] / fp64[k]["evals_per_s"] for k in KERNELS},
+        "fp32c_rel_err_vs_fp64": acc,
+        "fp64_sample": f"{FP64_SAMPLE_DIRS} of {D_HT} directions, all images",
+        "work": {"hybrid_terms_per_kernel": terms, "ect_updates": ect_updates, "lower_entries": n_lower,
+                 "algorithmic_extraction_bytes": ext_bytes},
+        "roofline": roof,
+        "e2e": {"value": terms * 3 / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "setup_s": setup_s,
+    }
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(imgs[0], dirs_ht_h, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(img, dirs_ht, budget_s: float = 20.0):
+    """The oracle as it stands, on a bounded sample: one image's tables, then hybrid
+    transforms of the three kernels over as many directions as fit the budget."""
+    import oracle as O
+    t0 = time.time()
+    tab = O.critical_tables(img)
+    t_tables = time.time() - t0
+    terms = 0
+    ndirs = 0
+    t1 = time.time()
+    half = 2
+    while time.time() - t1 < budget_s and ndirs < len(dirs_ht):
+        xi = dirs_ht[ndirs:ndirs + 1]
+        for k in KERNELS:
+            O.hybrid_transform(tab, k, xi)
+            o = O.orthant_of(xi[0])
+            r = o if o < half else O.partner(o, 2)
+            terms += len(tab.delta_idx[r])
+        ndirs += 1
+    t_ht = time.time() - t1
+    return {"value": terms / t_ht, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 image of {SIDE}x{SIDE}: tables in {t_tables:.1f} s, then {ndirs} directions x 3 kernels "
+                      f"({terms} terms) in {t_ht:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_info()
+    if rank != 0:
+        return
+    imgs = make_images(1, SIDE)
+    _, dirs_ht = make_dirs()
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    t0 = time.time()
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    samples = []
+    for _ in range(max(1, args.steps)):
+        s = cpu_baseline(imgs[0], dirs_ht, budget_s=per)
+        vals.append(s["value"])
+        samples.append(s["sample"])
+    wall = time.time() - t0
+    v = float(np.mean(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples[0]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--images", type=int, default=B_IMAGES)
+    p.add_argument("--side", type=int, default=SIDE)
+    p.add_argument("--cpu-budget", type=float, default=20.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
