@@ -133,26 +133,17 @@ def run_gpu(args):
     tabs = tb.tables_create(batch.shapes, batch.offsets)
     tabs.build(batch.pixels)
     tabs.sync()
-    n_delta = 0
-    n_lower = 0
-    for b in range(n_img):
-        for o in range(4):
-            nl, nd, _ = tabs.info(b, o)
-            n_lower += nl
-            n_delta += nd   # Delta table of o's representative: the table each direction of o uses
-    # evaluations per step: every direction of orthant o runs over |Delta_rep(o)| points
+    # table sizes: nl[b, o] = |Delta^-_o|, nd[b, o] = |Delta_rep(o)| (the table direction o uses)
+    nl = np.array([[tabs.info(b, o)[0] for o in range(4)] for b in range(n_img)], dtype=np.int64)
+    nd = np.array([[tabs.info(b, o)[1] for o in range(4)] for b in range(n_img)], dtype=np.int64)
     orth = np.array([sum(1 << k for k in range(2) if x[k] < 0) for x in dirs_ht_h])
-    terms = 0
-    for b in range(n_img):
-        for o in range(4):
-            terms += int(np.count_nonzero(orth == o)) * tabs.info(b, o)[1]
-    ect_updates = 0
     orth_e = np.array([sum(1 << k for k in range(2) if x[k] < 0) for x in dirs_ect_h])
-    for b in range(n_img):
-        for o in range(4):
-            ect_updates += int(np.count_nonzero(orth_e == o)) * tabs.info(b, o)[0]
-    seg_entries = sum(tabs.info(b, o)[0] for b in range(n_img) for o in range(4)) + \
-        sum(tabs.info(b, r)[1] for b in range(n_img) for r in range(2))
+    cnt_ht = np.bincount(orth, minlength=4)
+    cnt_ect = np.bincount(orth_e, minlength=4)
+    terms = int((nd * cnt_ht[None, :]).sum())            # evaluations per kernel per step
+    ect_updates = int((nl * cnt_ect[None, :]).sum())
+    n_lower = int(nl.sum())
+    seg_entries = n_lower + int(nd[:, :2].sum())         # 4 lower tables + 2 Delta tables per image
     ext_bytes = batch.pixels.numel() * 1 + seg_entries * 6      # u8 in, int32 idx + int16 value out
 
     ect_out = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
@@ -204,10 +195,7 @@ def run_gpu(args):
 
     # ---- plain FP64 hybrid path on a direction sample ---------------------------------------
     sample = dirs_ht[:FP64_SAMPLE_DIRS].contiguous()
-    sample_terms = 0
-    for b in range(n_img):
-        for o in range(4):
-            sample_terms += int(np.count_nonzero(orth[:FP64_SAMPLE_DIRS] == o)) * tabs.info(b, o)[1]
+    sample_terms = int((nd * np.bincount(orth[:FP64_SAMPLE_DIRS], minlength=4)[None, :]).sum())
     fp64 = {}
     fp32_s = {}
     for k in KERNELS:

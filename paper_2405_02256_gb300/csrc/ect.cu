@@ -27,8 +27,8 @@
 
 namespace topot {
 
-constexpr int kHistBlock = 256;
-constexpr int kHistSub = 2048;   // staged critical points per round
+constexpr int kHistBlock = 512;
+constexpr int kHistSub = 1024;   // staged critical points per round
 
 struct DirCoef {
     float a0, a1, a2, beta, delta;
@@ -86,7 +86,7 @@ __device__ __noinline__ int exact_bin(float c0, float c1, float c2, const double
 }
 
 template <int NDIM, int TD, typename Tval>
-__global__ void __launch_bounds__(kHistBlock) k_hist(EvalPlan P, TablesDev t, int32_t* out_lo,
+__global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t, int32_t* out_lo,
                                                      int32_t* out_hi) {
     constexpr int NW = kHistBlock / 32;
     constexpr int G = 32 / TD;
@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(kHistBlock) k_hist(EvalPlan P, TablesDev t, in
     int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [TD][T + 1]
     __shared__ long long sh_item;
     __shared__ int sh_dir[TD];
+    __shared__ int sh_amb_it[NW][kHistSub / NW];          // deferred exact binning, per warp
+    __shared__ unsigned sh_amb_mask[NW][kHistSub / NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = P.T;
@@ -156,30 +158,58 @@ __global__ void __launch_bounds__(kHistBlock) k_hist(EvalPlan P, TablesDev t, in
                                        (float)(2 * i2 - (I.m[2] - 1)), __int_as_float(v));
             }
             __syncthreads();
-            if (dvalid) {
+            {
                 const int per = (cnt + NW - 1) / NW;
                 const int ws = warp * per;
                 const int we = min(cnt, ws + per);
-                const int len = we - ws;
+                const int len = max(0, we - ws);
                 const int gl = (len + G - 1) / G;
                 const int gs = ws + g * gl;
                 const int ge = min(we, gs + gl);
                 int* row = const_cast<int*>(hrow);
-                for (int e = gs; e < ge; ++e) {
-                    const float4 q = stage[e];
+                const float umax = (float)T - 0.5f;
+                // Bin from u without float->int conversions: adding 1.5 * 2^23 rounds u to
+                // an integer r (ties to even) held in the low mantissa bits.  u is clamped to
+                // [-0.5, T - 0.5] first, so the sublevel bin ceil(u) and the superlevel index
+                // floor(u) + 1 both land in [0, T].  Points within delta of a bin edge are
+                // listed per warp and binned exactly after the loop.
+                int namb = 0;
+#pragma unroll 4
+                for (int it = 0; it < gl; ++it) {
+                    const int e = gs + it;
+                    const bool act = dvalid && e < ge;
+                    const float4 q = stage[act ? e : 0];
                     float u;
                     if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
                     else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
-                    int bin;
-                    if (fabsf(u - rintf(u)) < cf.delta) {
-                        bin = maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi, I.m, P.thr, T, u)
-                                     : exact_bin<NDIM, false>(q.x, q.y, q.z, xi, I.m, P.thr, T, u);
-                    } else {
-                        const float uc = fminf(fmaxf(u, -1.0f), (float)T);
-                        bin = maxbin ? (int)floorf(uc) + 1 : (int)ceilf(uc);
-                        bin = min(max(bin, 0), T);
+                    const float uc = fminf(fmaxf(u, -0.5f), umax);
+                    const float f = uc + 12582912.0f;
+                    const float rf = f - 12582912.0f;
+                    const int r = __float_as_int(f) - 0x4B400000;
+                    const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
+                    const bool amb = act && !(fabsf(u - rf) >= cf.delta);
+                    if (act && !amb) atomicAdd(&row[bin], __float_as_int(q.w));
+                    const unsigned ab = __ballot_sync(0xffffffffu, amb);
+                    if (ab) {
+                        if (lane == 0) {
+                            sh_amb_it[warp][namb] = it;
+                            sh_amb_mask[warp][namb] = ab;
+                        }
+                        ++namb;
                     }
-                    atomicAdd(&row[bin], __float_as_int(q.w));
+                }
+                __syncwarp();
+                for (int k = 0; k < namb; ++k) {
+                    if (sh_amb_mask[warp][k] & (1u << lane)) {
+                        const int e = gs + sh_amb_it[warp][k];
+                        const float4 q = stage[e];
+                        float u;
+                        if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
+                        else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
+                        const int bin = maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi, I.m, P.thr, T, u)
+                                               : exact_bin<NDIM, false>(q.x, q.y, q.z, xi, I.m, P.thr, T, u);
+                        atomicAdd(&row[bin], __float_as_int(q.w));
+                    }
                 }
             }
         }
@@ -244,6 +274,9 @@ static cudaError_t launch_hist_n(const EvalPlan& P, const TablesDev& t, int td, 
     case TDV: {                                                                                \
         auto k = k_hist<NDIM, TDV, Tval>;                                                      \
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        if (e == cudaSuccess)                                                                  \
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,        \
+                                     cudaSharedmemCarveoutMaxShared);                          \
         if (e != cudaSuccess) return e;                                                        \
         k<<<grid, kHistBlock, smem, st>>>(P, t, lo, hi);                                       \
         break;                                                                                 \

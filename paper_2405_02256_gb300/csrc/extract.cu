@@ -75,7 +75,7 @@ __device__ __forceinline__ void lower_star(const Tin* c, int rs, int ps, int (&o
 }
 
 template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
-__global__ void __launch_bounds__(BLOCK) k_extract(ExtractArgs p) {
+__global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
     using PT = PixTraits<Tin>;
     constexpr int NO = 1 << NDIM;              // orthants
     constexpr int S = NO + NO / 2;             // segments
@@ -188,8 +188,8 @@ __global__ void __launch_bounds__(BLOCK) k_extract(ExtractArgs p) {
 
     // ---- 2. lower-star values, kept in registers --------------------------------------
     int vals[K][NO];
-    long long chi_acc = 0;
-    long long abs_acc[NO];
+    int chi_acc = 0;          // |Delta^-| <= 2^n * 2^26 per vertex: K vertices fit int32 for u8,
+    int abs_acc[NO];          // and int32 input is limited to |phi| < 2^26 (checked below)
 #pragma unroll
     for (int o = 0; o < NO; ++o) abs_acc[o] = 0;
     bool bad_pixel = false;
@@ -229,15 +229,16 @@ __global__ void __launch_bounds__(BLOCK) k_extract(ExtractArgs p) {
             if (lane == 0) sh_cnt[(s * K + k) * NW + warp] = __popc(bal);
         }
     }
-    // chi and sum |Delta^-| of the tile
-    chi_acc = warp_sum(chi_acc);
+    // chi and sum |Delta^-| of the tile (64-bit from the warp level up)
+    const long long chi_w = warp_sum((long long)chi_acc);
+    long long abs_w[NO];
 #pragma unroll
-    for (int o = 0; o < NO; ++o) abs_acc[o] = warp_sum(abs_acc[o]);
+    for (int o = 0; o < NO; ++o) abs_w[o] = warp_sum((long long)abs_acc[o]);
     if (lane == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[0]), (unsigned long long)chi_acc);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[0]), (unsigned long long)chi_w);
 #pragma unroll
         for (int o = 0; o < NO; ++o)
-            atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[1 + o]), (unsigned long long)abs_acc[o]);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sh_acc[1 + o]), (unsigned long long)abs_w[o]);
     }
     __syncthreads();
 
@@ -318,6 +319,8 @@ template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
 static cudaError_t launch_extract_t(const ExtractArgs& a, size_t smem, cudaStream_t st) {
     auto kern = k_extract<NDIM, Tin, Tval, BLOCK, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)a.num_tiles, BLOCK, smem, st>>>(a);
     return cudaGetLastError();

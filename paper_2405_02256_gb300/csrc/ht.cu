@@ -41,7 +41,7 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float term) {
 // J0(x) = sum_k (-y)^k / (k!)^2, y = x^2 / 4 <= 1; truncation after k = 9 < 1e-13.
 __device__ __forceinline__ float j0_series_f(float x) {
     const float y = 0.25f * x * x;
-    float p = 1.0f / 13168189440000.0f;          // k = 9: 1 / (9!)^2
+    float p = 1.0f / 131681894400.0f;            // k = 9: 1 / (9!)^2
     p = fmaf(p, -y, 1.0f / 1625702400.0f);        // k = 8
     p = fmaf(p, -y, 1.0f / 25401600.0f);          // k = 7
     p = fmaf(p, -y, 1.0f / 518400.0f);            // k = 6
@@ -56,7 +56,7 @@ __device__ __forceinline__ float j0_series_f(float x) {
 // J1 for |x| <= 2 (A&S 9.1.10): J1(x) = (x/2) sum_k (-y)^k / (k! (k+1)!).
 __device__ __forceinline__ float j1_series_f(float x) {
     const float y = 0.25f * x * x;
-    float p = 1.0f / 131681894400.0f;             // k = 9: 1 / (9! 10!)
+    float p = 1.0f / 1316818944000.0f;            // k = 9: 1 / (9! 10!)
     p = fmaf(p, -y, 1.0f / 14631321600.0f);       // k = 8
     p = fmaf(p, -y, 1.0f / 203212800.0f);         // k = 7
     p = fmaf(p, -y, 1.0f / 3628800.0f);           // k = 6
@@ -128,7 +128,7 @@ __device__ __forceinline__ HtItem ht_item(const EvalPlan& P, const TablesDev& t,
 // Stage critical points [e0, e0 + cnt) as lattice data: A = (p0, p1, p2, value) with
 // p = q (LAPLACE: q_k = i_k - (m_k - 1) if eps_k = +1 else -i_k) or c_k = 2 i_k - (m_k - 1);
 // X = (x0, x1, x2) embedding coordinates (adjoint only).
-template <int NDIM, int KERNEL, bool WITH_X, typename Tval>
+template <int NDIM, int KERNEL, bool WITH_X, typename Tval, bool PACKED = false>
 __device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, long long e0, int cnt,
                                          float4* A, float4* X) {
     const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
@@ -156,7 +156,12 @@ __device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, l
                 p[k] = c[k];
         }
         if (NDIM == 2) p[2] = 0.0f;
-        A[i] = make_float4(p[0], p[1], p[2], v);
+        if (PACKED) {
+            A[2 * i] = make_float4(p[0], p[0], p[1], p[1]);
+            A[2 * i + 1] = make_float4(p[2], p[2], v, v);
+        } else {
+            A[i] = make_float4(p[0], p[1], p[2], v);
+        }
         if (WITH_X) {
             float x[3];
 #pragma unroll
@@ -184,13 +189,118 @@ __device__ __forceinline__ void ht_dir(const EvalPlan& P, const HtItem& it, int 
 
 // ---- forward, FP32 compensated ------------------------------------------------------------
 
+// Packed FP32 pairs (f32x2: one instruction operates on two directions).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// cos z from its Taylor series as a polynomial in w = z^2 through w^DEG:
+// DEG = 5 for |z| <= 0.75 (truncation < 1e-10), DEG = 7 for |z| <= 1.75 (< 4e-10).
+template <int DEG>
+__device__ __forceinline__ float2 cos_poly2(float2 w) {
+    // (-1)^k / (2k)!
+    constexpr float c[8] = {1.0f, -0.5f, 1.0f / 24.0f, -1.0f / 720.0f, 1.0f / 40320.0f, -1.0f / 3628800.0f,
+                            1.0f / 479001600.0f, -1.0f / 87178291200.0f};
+    float2 p = make_float2(c[DEG], c[DEG]);
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) p = fma2(p, w, make_float2(c[k], c[k]));
+    return p;
+}
+
+// Compensated add of a block sum x into (s, nc) for two sums at once.
+__device__ __forceinline__ void kahan2_add(float2& s, float2& nc, float2 x) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 y = add2(x, nc);
+    const float2 t = add2(s, y);
+    const float2 u = fma2(s, m1, t);
+    nc = fma2(u, m1, y);
+    s = t;
+}
+
+// J0 from its ascending series in y = (z/2)^2 (A&S 9.1.10), through y^DEG.
+// DEG = 5 for |z| <= 1 (truncation < 5e-10), DEG = 9 for |z| <= 2 (< 1e-13).
+template <int DEG>
+__device__ __forceinline__ float2 j0_poly2(float2 y) {
+    // (-1)^k / (k!)^2
+    constexpr float c[10] = {1.0f, -1.0f, 1.0f / 4.0f, -1.0f / 36.0f, 1.0f / 576.0f, -1.0f / 14400.0f,
+                             1.0f / 518400.0f, -1.0f / 25401600.0f, 1.0f / 1625702400.0f,
+                             -1.0f / 131681894400.0f};
+    float2 p = make_float2(c[DEG], c[DEG]);
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) p = fma2(p, y, make_float2(c[k], c[k]));
+    return p;
+}
+
+// Kernel value for a direction pair on the packed paths.
+template <int KERNEL, int PATH>
+__device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2]) {
+    if (KERNEL == TOPOT_LAPLACE) {
+        k[0] = make_float2(ex2_approx(z.x), ex2_approx(z.y));
+    } else if (KERNEL == TOPOT_FOURIER) {
+        k[0] = make_float2(__sinf(z.x), __sinf(z.y));
+        k[1] = PATH == 2 ? cos_poly2<5>(mul2(z, z)) : cos_poly2<7>(mul2(z, z));
+    } else {
+        const float2 y = mul2(z, z);   // z is already halved
+        k[0] = PATH == 3 ? j0_poly2<4>(y) : (PATH == 2 ? j0_poly2<5>(y) : j0_poly2<9>(y));
+    }
+}
+
+// Packed evaluation of staged points [ws, we) for NPR direction pairs.  Terms are
+// summed by FMA in blocks of four, and each block sum is added with compensation:
+// a block adds at most 4 eps of its terms' magnitudes, the compensated sum 2 eps.
+template <int NDIM, int KERNEL, int NPR, int PATH>
+__device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we, const float2 (&w)[NPR][3],
+                                                float2 (&s2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1],
+                                                float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
+    constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
+    constexpr int BLK = 4;
+    int e = ws;
+    for (; e < we; e += BLK) {
+        const int nb = min(BLK, we - e);
+        float2 blk[NPR][NC];
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) {
+            if (u < nb) {
+                const float4 qa = A[2 * (e + u)];
+                const float4 qb = A[2 * (e + u) + 1];
+                const float2 c0 = make_float2(qa.x, qa.y), c1 = make_float2(qa.z, qa.w);
+                const float2 c2 = make_float2(qb.x, qb.y), v2 = make_float2(qb.z, qb.w);
+#pragma unroll
+                for (int pq = 0; pq < NPR; ++pq) {
+                    float2 z = mul2(c0, w[pq][0]);
+                    z = fma2(c1, w[pq][1], z);
+                    if (NDIM == 3) z = fma2(c2, w[pq][2], z);
+                    float2 k[2];
+                    kernel_pair<KERNEL, PATH>(z, k);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) blk[pq][c] = u == 0 ? mul2(v2, k[c]) : fma2(v2, k[c], blk[pq][c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int pq = 0; pq < NPR; ++pq)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) kahan2_add(s2[pq][c], n2[pq][c], blk[pq][c]);
+    }
+}
+
 template <int NDIM, int KERNEL, int DL, typename Tval>
 __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, double* part) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr int TDH = 32 * DL;
     constexpr int NO = 1 << NDIM;
-    __shared__ float4 A[kHtSub];
-    __shared__ double red[kHtWarps][TDH * NC];
+    constexpr int NPR = DL / 2;                 // direction pairs per lane (packed path)
+    // staging buffer: scalar path (p0, p1, p2, value) per point; packed path
+    // (p0, p0, p1, p1), (p2, p2, v, v); reused for the per-item reduction
+    __shared__ __align__(16) float4 A[2 * kHtSub];
+    static_assert(sizeof(double) * kHtWarps * TDH * NC <= sizeof(float4) * 2 * kHtSub, "reduction buffer");
+    double(*red)[TDH * NC] = reinterpret_cast<double(*)[TDH * NC]>(A);
     __shared__ long long sh_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long nitems = P.ctl[2];
@@ -204,47 +314,109 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
         int tile;
         const HtItem it = ht_item(P, t, item, NO, TDH, tile);
         HtDir hd[DL];
+        float mloc = 0.0f;   // max over this lane's directions of sum |xi_k| / 2 >= |<xi, v>|
 #pragma unroll
-        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+        for (int j = 0; j < DL; ++j) {
+            ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+            if (hd[j].valid)
+                mloc = fmaxf(mloc, (float)(0.5 * (fabs(hd[j].xi[0]) + fabs(hd[j].xi[1]) + fabs(hd[j].xi[2]))));
+        }
+        // tile-uniform choice of the evaluation path (all warps see the same tile)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+        // 0: scalar generic path; packed paths by the range of |<xi, v>| <= mloc:
+        //   Fourier: 1 (<= 1.75, cos through w^7), 2 (<= 0.75, cos through w^5)
+        //   Bessel:  1 (<= 2, J0 through y^9), 2 (<= 1, y^5), 3 (<= 0.75, y^4)
+        int path = 0;
+        if (NPR > 0) {
+            if (KERNEL == TOPOT_LAPLACE) path = 1;
+            else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
+            else path = mloc <= 0.75f ? 3 : (mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0));
+        }
+
         float acc[DL][NC], cmp[DL][NC];
 #pragma unroll
         for (int j = 0; j < DL; ++j)
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
 
-        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
-            const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
-            __syncthreads();
-            ht_stage<NDIM, KERNEL, false, Tval>(t, it, e0, cnt, A, nullptr);
-            __syncthreads();
-            const int per = (cnt + kHtWarps - 1) / kHtWarps;
-            const int ws = warp * per, we = min(cnt, ws + per);
-            for (int e = ws; e < we; ++e) {
-                const float4 q = A[e];
+        if (path == 0) {
+            for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
+                const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
+                __syncthreads();
+                ht_stage<NDIM, KERNEL, false, Tval>(t, it, e0, cnt, A, nullptr);
+                __syncthreads();
+                const int per = (cnt + kHtWarps - 1) / kHtWarps;
+                const int ws = warp * per, we = min(cnt, ws + per);
+                for (int e = ws; e < we; ++e) {
+                    const float4 q = A[e];
 #pragma unroll
-                for (int j = 0; j < DL; ++j) {
-                    float z = q.x * hd[j].w[0];
-                    z = fmaf(q.y, hd[j].w[1], z);
-                    if (NDIM == 3) z = fmaf(q.z, hd[j].w[2], z);
-                    if (KERNEL == TOPOT_LAPLACE) {
-                        kahan_add(acc[j][0], cmp[j][0], q.w * exp2f(z));
-                    } else if (KERNEL == TOPOT_FOURIER) {
-                        float sn, cs;
-                        sincos_f(z, sn, cs);
-                        kahan_add(acc[j][0], cmp[j][0], q.w * sn);
-                        kahan_add(acc[j][1], cmp[j][1], q.w * cs);
-                    } else {
-                        kahan_add(acc[j][0], cmp[j][0], q.w * bessel_j0_f(z));
+                    for (int j = 0; j < DL; ++j) {
+                        float z = q.x * hd[j].w[0];
+                        z = fmaf(q.y, hd[j].w[1], z);
+                        if (NDIM == 3) z = fmaf(q.z, hd[j].w[2], z);
+                        if (KERNEL == TOPOT_LAPLACE) {
+                            kahan_add(acc[j][0], cmp[j][0], q.w * exp2f(z));
+                        } else if (KERNEL == TOPOT_FOURIER) {
+                            float sn, cs;
+                            sincos_f(z, sn, cs);
+                            kahan_add(acc[j][0], cmp[j][0], q.w * sn);
+                            kahan_add(acc[j][1], cmp[j][1], q.w * cs);
+                        } else {
+                            kahan_add(acc[j][0], cmp[j][0], q.w * bessel_j0_f(z));
+                        }
                     }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < DL; ++j)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cmp[j][c] = -cmp[j][c];   // report as s + nc
+        } else if constexpr (NPR > 0) {
+            // packed coefficients: pair p covers directions 2p and 2p + 1 of this lane;
+            // Bessel uses z / 2 so that y = (z / 2)^2 is one multiply
+            float2 w[NPR][3];
+            const float wsc = KERNEL == TOPOT_BESSEL ? 0.5f : 1.0f;
+#pragma unroll
+            for (int pq = 0; pq < NPR; ++pq)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w[pq][k] = make_float2(wsc * hd[2 * pq].w[k], wsc * hd[2 * pq + 1].w[k]);
+            float2 s2[NPR][NC], n2[NPR][NC];
+#pragma unroll
+            for (int pq = 0; pq < NPR; ++pq)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) s2[pq][c] = n2[pq][c] = make_float2(0.0f, 0.0f);
+
+            for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
+                const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
+                __syncthreads();
+                ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr);
+                __syncthreads();
+                const int per = (cnt + kHtWarps - 1) / kHtWarps;
+                const int ws = warp * per, we = min(cnt, ws + per);
+                switch (path) {
+                    case 1: ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2); break;
+                    case 2: ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2); break;
+                    default: ht_packed_range<NDIM, KERNEL, NPR, 3>(A, ws, we, w, s2, n2); break;
+                }
+            }
+#pragma unroll
+            for (int pq = 0; pq < NPR; ++pq)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    acc[2 * pq][c] = s2[pq][c].x;
+                    cmp[2 * pq][c] = n2[pq][c].x;
+                    acc[2 * pq + 1][c] = s2[pq][c].y;
+                    cmp[2 * pq + 1][c] = n2[pq][c].y;
+                }
         }
-        // fixed-order FP64 reduction over warps -> item partial
+        // fixed-order FP64 reduction over warps -> item partial (red aliases the stage)
+        __syncthreads();
 #pragma unroll
         for (int j = 0; j < DL; ++j)
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] - (double)cmp[j][c];
+                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] + (double)cmp[j][c];
         __syncthreads();
         for (int i = tid; i < TDH * NC; i += kHtBlock) {
             double s = 0.0;
