@@ -379,7 +379,8 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
     }
     const topot_tuning& u = *tuning;
     if ((u.ect_dirs_per_warp && u.ect_dirs_per_warp != 8 && u.ect_dirs_per_warp != 16 && u.ect_dirs_per_warp != 32) ||
-        (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4) ||
+        (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4 &&
+         u.ht_dirs_per_lane != 8) ||
         u.chunk < 0 || (u.chunk % 256) != 0 || u.ctas_per_sm < 0 || u.ctas_per_sm > 32)
         return fail(TOPOT_ERR_INVALID_ARG, "tables_set_tuning: value out of range");
     t->tuning = u;
@@ -487,7 +488,11 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     if (precision == TOPOT_FP32C) {
         dl = t->tuning.ht_dirs_per_lane;
         const int per_orthant = D / NO;
-        if (dl == 0) dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+        if (dl == 0) {
+            dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+            if (kernel == TOPOT_LAPLACE && per_orthant >= 256) dl = 8;
+        }
+        if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
         if (adjoint && dl > 2) dl = 2;
     }
     const int tdh = 32 * dl;

@@ -95,8 +95,6 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
     int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [TD][T + 1]
     __shared__ long long sh_item;
     __shared__ int sh_dir[TD];
-    __shared__ int sh_amb_it[NW][kHistSub / NW];          // deferred exact binning, per warp
-    __shared__ unsigned sh_amb_mask[NW][kHistSub / NW];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = P.T;
@@ -140,12 +138,27 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
         const long long e_end = min(N, e_begin + chunk);
         const int* hrow = hist + dl * HS;
 
+        // Staging is software-pipelined: the raw entries of the next round are loaded
+        // into registers while the current round is binned.
+        constexpr int PF = kHistSub / kHistBlock;     // entries per thread per round
+        uint32_t pidx[PF];
+        int pval[PF];
+        auto prefetch = [&](long long e0) {
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const long long e = e0 + tid + k * kHistBlock;
+                pidx[k] = e < e_end ? (uint32_t)t.arena_idx[base + e] : 0u;
+                pval[k] = e < e_end ? (int)aval[base + e] : 0;
+            }
+        };
+        prefetch(e_begin);
         for (long long e0 = e_begin; e0 < e_end; e0 += kHistSub) {
             const int cnt = (int)min((long long)kHistSub, e_end - e0);
             __syncthreads();
-            for (int i = tid; i < cnt; i += kHistBlock) {
-                const uint32_t idx = (uint32_t)t.arena_idx[base + e0 + i];
-                const int v = (int)aval[base + e0 + i];
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int i = tid + k * kHistBlock;
+                const uint32_t idx = pidx[k];
                 const uint32_t q1 = fastdiv(idx, I.div0);
                 const int i0 = (int)(idx - q1 * (uint32_t)I.m[0]);
                 int i1 = (int)q1, i2 = 0;
@@ -154,16 +167,20 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
                     i1 = (int)(q1 - q2 * (uint32_t)I.m[1]);
                     i2 = (int)q2;
                 }
+                // entries past the chunk end carry value 0 and add nothing
                 stage[i] = make_float4((float)(2 * i0 - (I.m[0] - 1)), (float)(2 * i1 - (I.m[1] - 1)),
-                                       (float)(2 * i2 - (I.m[2] - 1)), __int_as_float(v));
+                                       (float)(2 * i2 - (I.m[2] - 1)), __int_as_float(pval[k]));
             }
             __syncthreads();
+            if (e0 + kHistSub < e_end) prefetch(e0 + kHistSub);
             {
-                const int per = (cnt + NW - 1) / NW;
+                // rounds are padded with zero-value entries to a multiple of 4 per warp group
+                const int cnt4 = (cnt + 3) & ~3;
+                const int per = (((cnt4 + NW - 1) / NW) + 3) & ~3;
                 const int ws = warp * per;
-                const int we = min(cnt, ws + per);
+                const int we = min(cnt4, ws + per);
                 const int len = max(0, we - ws);
-                const int gl = (len + G - 1) / G;
+                const int gl = (((len + G - 1) / G) + 3) & ~3;
                 const int gs = ws + g * gl;
                 const int ge = min(we, gs + gl);
                 int* row = const_cast<int*>(hrow);
@@ -172,43 +189,42 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
                 // an integer r (ties to even) held in the low mantissa bits.  u is clamped to
                 // [-0.5, T - 0.5] first, so the sublevel bin ceil(u) and the superlevel index
                 // floor(u) + 1 both land in [0, T].  Points within delta of a bin edge are
-                // listed per warp and binned exactly after the loop.
-                int namb = 0;
-#pragma unroll 4
-                for (int it = 0; it < gl; ++it) {
-                    const int e = gs + it;
-                    const bool act = dvalid && e < ge;
-                    const float4 q = stage[act ? e : 0];
-                    float u;
-                    if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
-                    else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
-                    const float uc = fminf(fmaxf(u, -0.5f), umax);
-                    const float f = uc + 12582912.0f;
-                    const float rf = f - 12582912.0f;
-                    const int r = __float_as_int(f) - 0x4B400000;
-                    const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
-                    const bool amb = act && !(fabsf(u - rf) >= cf.delta);
-                    if (act && !amb) atomicAdd(&row[bin], __float_as_int(q.w));
-                    const unsigned ab = __ballot_sync(0xffffffffu, amb);
-                    if (ab) {
-                        if (lane == 0) {
-                            sh_amb_it[warp][namb] = it;
-                            sh_amb_mask[warp][namb] = ab;
-                        }
-                        ++namb;
-                    }
-                }
-                __syncwarp();
-                for (int k = 0; k < namb; ++k) {
-                    if (sh_amb_mask[warp][k] & (1u << lane)) {
-                        const int e = gs + sh_amb_it[warp][k];
-                        const float4 q = stage[e];
+                // binned exactly on a slow path, checked once per 4 points.
+                // Lanes of directions past the tile end bin into rows nobody reads.
+                for (int e = gs; e < ge; e += 4) {
+                    bool amb[4];
+                    bool any = false;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 q = stage[e + k];
                         float u;
                         if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
                         else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
-                        const int bin = maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi, I.m, P.thr, T, u)
-                                               : exact_bin<NDIM, false>(q.x, q.y, q.z, xi, I.m, P.thr, T, u);
-                        atomicAdd(&row[bin], __float_as_int(q.w));
+                        const float uc = fminf(fmaxf(u, -0.5f), umax);
+                        const float f = uc + 12582912.0f;
+                        const float rf = f - 12582912.0f;
+                        const int r = __float_as_int(f) - 0x4B400000;
+                        const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
+                        amb[k] = !(fabsf(u - rf) >= cf.delta);
+                        any |= amb[k];
+                        if (!amb[k]) atomicAdd(&row[bin], __float_as_int(q.w));
+                    }
+                    // rare: exact FP64 binning.  A per-lane branch: lane groups of one warp
+                    // may run different trip counts, so no warp-wide vote may be used here.
+                    if (any) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (amb[k]) {
+                                const float4 q = stage[e + k];
+                                float u;
+                                if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
+                                else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
+                                const int bin = maxbin
+                                                    ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi, I.m, P.thr, T, u)
+                                                    : exact_bin<NDIM, false>(q.x, q.y, q.z, xi, I.m, P.thr, T, u);
+                                atomicAdd(&row[bin], __float_as_int(q.w));
+                            }
+                        }
                     }
                 }
             }

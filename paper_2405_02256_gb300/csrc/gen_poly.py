@@ -1,0 +1,64 @@
+"""Derive the short polynomial kernels used by the FP32 hybrid-transform paths.
+
+Each function f is approximated on [0, X] by its degree-d Chebyshev interpolant (the
+classical Chebyshev-economisation route: interpolate at the d + 1 Chebyshev nodes of
+[0, X], then convert to the power basis).  f is evaluated from its own power series in
+exact rational arithmetic, so no library routine enters the constants:
+
+* J0(2 sqrt(y)) = sum_k (-y)^k / (k!)^2            (Abramowitz & Stegun 9.1.10)
+* cos(sqrt(w))  = sum_k (-w)^k / (2k)!
+
+The script prints the FP32 constants (copied into ht.cu) and the worst absolute error of
+an FP32 Horner evaluation with fused multiply-adds on a fine grid.
+
+Run:  python paper_2405_02256_gb300/csrc/gen_poly.py
+"""
+from fractions import Fraction
+from math import comb, cos, factorial, pi
+
+import numpy as np
+
+
+def series(kind: str, x: Fraction, terms: int = 40) -> Fraction:
+    s = Fraction(0)
+    p = Fraction(1)
+    for k in range(terms):
+        den = factorial(k) ** 2 if kind == "j0" else factorial(2 * k)
+        s += p / den
+        p *= -x
+    return s
+
+
+def cheb_power_coeffs(kind: str, X: float, deg: int):
+    """Power-basis coefficients (in x) of the Chebyshev interpolant on [0, X]."""
+    n = deg + 1
+    nodes = [0.5 * X * (1 + cos(pi * (2 * j + 1) / (2 * n))) for j in range(n)]
+    vals = [float(series(kind, Fraction(t))) for t in nodes]
+    # Vandermonde solve in exact-ish float64 on the scaled variable t = x / X
+    V = np.array([[(t / X) ** k for k in range(n)] for t in nodes], dtype=np.float64)
+    a = np.linalg.solve(V, np.array(vals))
+    return [a[k] / X ** k for k in range(n)]
+
+
+def horner_f32(c, x):
+    x = np.float32(x)
+    p = np.float32(c[-1])
+    for ck in reversed(c[:-1]):
+        p = np.float32(np.float64(p) * np.float64(x) + np.float64(np.float32(ck)))   # fma, one rounding
+    return p
+
+
+def report(kind: str, X: float, deg: int):
+    c = cheb_power_coeffs(kind, X, deg)
+    c32 = [np.float32(v) for v in c]
+    xs = np.linspace(0.0, X, 20001)
+    err = max(abs(float(horner_f32(c32, x)) - float(series(kind, Fraction(float(np.float32(x)))))) for x in xs[::20])
+    print(f"{kind} on [0, {X}] degree {deg}: max |error| of FP32 Horner = {err:.3e}")
+    print("   {" + ", ".join(f"{float(v):.9e}f" for v in c32) + "}")
+
+
+if __name__ == "__main__":
+    report("j0", 0.25, 3)       # |z| <= 1
+    report("j0", 1.0, 5)        # |z| <= 2
+    report("cos", 0.5625, 3)    # |z| <= 0.75
+    report("cos", 3.0625, 5)    # |z| <= 1.75

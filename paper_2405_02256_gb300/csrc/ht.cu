@@ -200,17 +200,39 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// cos z from its Taylor series as a polynomial in w = z^2 through w^DEG:
-// DEG = 5 for |z| <= 0.75 (truncation < 1e-10), DEG = 7 for |z| <= 1.75 (< 4e-10).
-template <int DEG>
-__device__ __forceinline__ float2 cos_poly2(float2 w) {
-    // (-1)^k / (2k)!
-    constexpr float c[8] = {1.0f, -0.5f, 1.0f / 24.0f, -1.0f / 720.0f, 1.0f / 40320.0f, -1.0f / 3628800.0f,
-                            1.0f / 479001600.0f, -1.0f / 87178291200.0f};
-    float2 p = make_float2(c[DEG], c[DEG]);
+// Short polynomial kernels: degree-d Chebyshev interpolants on [0, X] written in the
+// power basis (constants derived by gen_poly.py from the functions' own series; the
+// listed bounds are the worst absolute errors of the FP32 Horner evaluation).
+//   cos(sqrt w): X = 0.5625 (|z| <= 0.75), d = 3, 8e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
+//   J0(2 sqrt y): X = 0.25 (|z| <= 1), d = 3, 9e-8;       X = 1 (|z| <= 2), d = 5, 5e-8
+template <int N>
+__device__ __forceinline__ float2 horner2(const float (&c)[N], float2 x) {
+    float2 p = make_float2(c[N - 1], c[N - 1]);
 #pragma unroll
-    for (int k = DEG - 1; k >= 0; --k) p = fma2(p, w, make_float2(c[k], c[k]));
+    for (int k = N - 2; k >= 0; --k) p = fma2(p, x, make_float2(c[k], c[k]));
     return p;
+}
+
+__device__ __forceinline__ float2 cos_short2(float2 w) {
+    constexpr float c[4] = {1.000000000e+00f, -4.999988973e-01f, 4.165696725e-02f, -1.361225732e-03f};
+    return horner2(c, w);
+}
+
+__device__ __forceinline__ float2 cos_long2(float2 w) {
+    constexpr float c[6] = {1.000000000e+00f, -4.999999702e-01f, 4.166659340e-02f, -1.388788689e-03f,
+                            2.473820496e-05f, -2.569863113e-07f};
+    return horner2(c, w);
+}
+
+__device__ __forceinline__ float2 j0_short2(float2 y) {
+    constexpr float c[4] = {9.999999404e-01f, -9.999933243e-01f, 2.498667836e-01f, -2.692156099e-02f};
+    return horner2(c, y);
+}
+
+__device__ __forceinline__ float2 j0_long2(float2 y) {
+    constexpr float c[6] = {1.000000000e+00f, -9.999999404e-01f, 2.499992549e-01f, -2.777458727e-02f,
+                            1.729921903e-03f, -6.387370377e-05f};
+    return horner2(c, y);
 }
 
 // Compensated add of a block sum x into (s, nc) for two sums at once.
@@ -223,43 +245,32 @@ __device__ __forceinline__ void kahan2_add(float2& s, float2& nc, float2 x) {
     s = t;
 }
 
-// J0 from its ascending series in y = (z/2)^2 (A&S 9.1.10), through y^DEG.
-// DEG = 5 for |z| <= 1 (truncation < 5e-10), DEG = 9 for |z| <= 2 (< 1e-13).
-template <int DEG>
-__device__ __forceinline__ float2 j0_poly2(float2 y) {
-    // (-1)^k / (k!)^2
-    constexpr float c[10] = {1.0f, -1.0f, 1.0f / 4.0f, -1.0f / 36.0f, 1.0f / 576.0f, -1.0f / 14400.0f,
-                             1.0f / 518400.0f, -1.0f / 25401600.0f, 1.0f / 1625702400.0f,
-                             -1.0f / 131681894400.0f};
-    float2 p = make_float2(c[DEG], c[DEG]);
-#pragma unroll
-    for (int k = DEG - 1; k >= 0; --k) p = fma2(p, y, make_float2(c[k], c[k]));
-    return p;
-}
-
-// Kernel value for a direction pair on the packed paths.
+// Fourier: sin always on the MUFU pipe; cos on the MUFU pipe for odd pairs and as a
+// polynomial on the FMA pipe for even pairs, which balances the two pipes.
 template <int KERNEL, int PATH>
-__device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2]) {
+__device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_cos) {
     if (KERNEL == TOPOT_LAPLACE) {
         k[0] = make_float2(ex2_approx(z.x), ex2_approx(z.y));
     } else if (KERNEL == TOPOT_FOURIER) {
         k[0] = make_float2(__sinf(z.x), __sinf(z.y));
-        k[1] = PATH == 2 ? cos_poly2<5>(mul2(z, z)) : cos_poly2<7>(mul2(z, z));
+        if (mufu_cos) k[1] = make_float2(__cosf(z.x), __cosf(z.y));
+        else k[1] = PATH == 2 ? cos_short2(mul2(z, z)) : cos_long2(mul2(z, z));
     } else {
         const float2 y = mul2(z, z);   // z is already halved
-        k[0] = PATH == 3 ? j0_poly2<4>(y) : (PATH == 2 ? j0_poly2<5>(y) : j0_poly2<9>(y));
+        k[0] = PATH == 2 ? j0_short2(y) : j0_long2(y);
     }
 }
 
 // Packed evaluation of staged points [ws, we) for NPR direction pairs.  Terms are
-// summed by FMA in blocks of four, and each block sum is added with compensation:
-// a block adds at most 4 eps of its terms' magnitudes, the compensated sum 2 eps.
+// summed by FMA in blocks of BLK points (8, or 4 for Fourier whose MUFU sin/cos carry
+// more error), and each block sum is added with compensation: a block adds at most
+// BLK eps of its terms' magnitudes, the compensated sum 2 eps.
 template <int NDIM, int KERNEL, int NPR, int PATH>
 __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we, const float2 (&w)[NPR][3],
                                                 float2 (&s2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1],
                                                 float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
-    constexpr int BLK = 4;
+    constexpr int BLK = KERNEL == TOPOT_FOURIER ? 4 : 8;
     int e = ws;
     for (; e < we; e += BLK) {
         const int nb = min(BLK, we - e);
@@ -277,7 +288,7 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
                     z = fma2(c1, w[pq][1], z);
                     if (NDIM == 3) z = fma2(c2, w[pq][2], z);
                     float2 k[2];
-                    kernel_pair<KERNEL, PATH>(z, k);
+                    kernel_pair<KERNEL, PATH>(z, k, (pq & 1) == 1);
 #pragma unroll
                     for (int c = 0; c < NC; ++c) blk[pq][c] = u == 0 ? mul2(v2, k[c]) : fma2(v2, k[c], blk[pq][c]);
                 }
@@ -325,13 +336,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
         // 0: scalar generic path; packed paths by the range of |<xi, v>| <= mloc:
-        //   Fourier: 1 (<= 1.75, cos through w^7), 2 (<= 0.75, cos through w^5)
-        //   Bessel:  1 (<= 2, J0 through y^9), 2 (<= 1, y^5), 3 (<= 0.75, y^4)
+        //   Fourier: 2 (<= 0.75, short cos), 1 (<= 1.75, long cos)
+        //   Bessel:  2 (<= 1, short J0), 1 (<= 2, long J0)
         int path = 0;
         if (NPR > 0) {
             if (KERNEL == TOPOT_LAPLACE) path = 1;
             else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
-            else path = mloc <= 0.75f ? 3 : (mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0));
+            else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
         }
 
         float acc[DL][NC], cmp[DL][NC];
@@ -394,11 +405,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
                 __syncthreads();
                 const int per = (cnt + kHtWarps - 1) / kHtWarps;
                 const int ws = warp * per, we = min(cnt, ws + per);
-                switch (path) {
-                    case 1: ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2); break;
-                    case 2: ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2); break;
-                    default: ht_packed_range<NDIM, KERNEL, NPR, 3>(A, ws, we, w, s2, n2); break;
-                }
+                if (path == 2) ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2);
+                else ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2);
             }
 #pragma unroll
             for (int pq = 0; pq < NPR; ++pq)
@@ -772,6 +780,10 @@ static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precis
             case 1: k_ht_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
             case 2: k_ht_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
             case 4: k_ht_f32<NDIM, KERNEL, 4, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 8:
+                if (KERNEL != TOPOT_LAPLACE) return cudaErrorInvalidValue;
+                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                break;
             default: return cudaErrorInvalidValue;
         }
     }
