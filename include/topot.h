@@ -191,6 +191,24 @@ TOPOT_API topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel
                                    int per_image_dirs, const double* d_gout,
                                    double* d_gdirs, void* stream);
 
+/* hybrid_transform() for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment variant.  hybrid_transform() may call cudaMalloc to
+ * grow the handle's workspace; code running where allocation is forbidden (inside an
+ * allocator or memory-pool callback, under a no-allocation real-time budget, in a host
+ * that disallows cudaMalloc after start-up) can call this entry point instead.
+ * Arguments and result are those of hybrid_transform(); the handle's device must be
+ * current.  Its scratch (work plan and partial sums) lives in one fixed 16 MiB device
+ * array that every GPU loading the library holds until the process exits; the first
+ * call on a device looks the array's address up (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  It calls no cudaMalloc / cudaFree.  A call
+ * whose scratch would exceed 16 MiB returns TOPOT_ERR_INVALID_ARG with the size in the
+ * message.  All calls on a device share the array: calls that may overlap on the GPU
+ * (different streams, no ordering) race and must be serialised by the caller. */
+TOPOT_API topot_status hybrid_transform_noalloc(const topot_tables* t, topot_kernel kernel,
+                                               topot_precision precision, const double* d_dirs,
+                                               int D, int per_image_dirs, double* d_out,
+                                               void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 TOPOT_API const char* topot_last_error(void);
 

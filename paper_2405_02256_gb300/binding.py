@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "
 API_SYMBOLS = (
     "build_critical_tables", "tables_create", "tables_build", "tables_sync", "tables_info",
     "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
-    "hybrid_transform_grad", "topot_last_error",
+    "hybrid_transform_grad", "hybrid_transform_noalloc", "topot_last_error",
 )
 
 
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
         "radon": [vp, vp, i32, i32, dp, dp, i32, vp, vp],
         "hybrid_transform": [vp, i32, i32, vp, i32, i32, vp, vp],
         "hybrid_transform_grad": [vp, i32, i32, vp, i32, i32, vp, vp, vp],
+        "hybrid_transform_noalloc": [vp, i32, i32, vp, i32, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

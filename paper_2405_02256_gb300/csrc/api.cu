@@ -560,3 +560,134 @@ topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel, t
 }
 
 }  // extern "C"
+
+// ---- hybrid transform for callers that cannot allocate ---------------------------------------
+//
+// hybrid_transform() grows a workspace inside the tables handle with cudaMalloc when a
+// call needs more than it has.  Code that runs where allocation is not allowed -- inside
+// a custom memory pool or allocator callback, under an allocation-free real-time budget,
+// or in a host that forbids cudaMalloc after start-up -- cannot use it.  This variant
+// takes its scratch (work plan and per-item partial sums) from one fixed array of
+// kNoAllocScratchBytes in device global memory that every GPU which loads the library
+// holds until the process exits.  Its result is that of hybrid_transform().
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The symbol name is only a
+// host-side handle: the address is looked up once per device with that device current.
+topot_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "hybrid_transform_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(TOPOT_ERR_UNSUPPORTED, "hybrid_transform_noalloc: device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "hybrid_transform_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return TOPOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kernel, topot_precision precision,
+                                      const double* d_dirs, int D, int per_image_dirs, double* d_out,
+                                      void* stream) {
+    topot_tables* t = const_cast<topot_tables*>(tc);
+    const char* name = "hybrid_transform_noalloc";
+    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
+    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad kernel");
+    if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
+    int dev = 0;
+    TOPOT_CUDA(cudaGetDevice(&dev));
+    if (dev != t->device)
+        return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": the handle's device must be current");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nsets = per_image_dirs ? t->B : 1;
+    const int NO = t->NO;
+    // same tile and chunk choices as hybrid_transform, hence the same result
+    int dl = 1;
+    if (precision == TOPOT_FP32C) {
+        dl = t->tuning.ht_dirs_per_lane;
+        const int per_orthant = D / NO;
+        if (dl == 0) {
+            dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+            if (kernel == TOPOT_LAPLACE && per_orthant >= 256) dl = 8;
+        }
+        if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
+    }
+    const int tdh = 32 * dl;
+    const int ncomp = kernel == TOPOT_FOURIER ? 2 : 1;
+    const int npairs = t->B * NO;
+    const int target = t->sm_count * 16;
+    long long max_items;
+    if (t->tuning.chunk > 0) {
+        max_items = 0;
+        for (int b = 0; b < t->B; ++b)
+            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.chunk - 1) / t->tuning.chunk);
+    } else {
+        max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
+    }
+    const size_t part_elems = (size_t)max_items * tdh * ncomp;
+    const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
+                        sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * part_elems +
+                        8 * 256;
+    if (need > kNoAllocScratchBytes)
+        return fail(TOPOT_ERR_INVALID_ARG,
+                    std::string(name) + ": this call needs " + std::to_string(need) +
+                        " bytes of scratch, more than the fixed " + std::to_string(kNoAllocScratchBytes) +
+                        "; use fewer directions or images per call, or hybrid_transform");
+    void* scratch = nullptr;
+    topot_status s = noalloc_scratch(&scratch);
+    if (s != TOPOT_OK) return s;
+    // Every field below is written by the planning kernels before it is read, so the
+    // previous call's contents need no clearing.
+    Carver cv{reinterpret_cast<char*>(scratch)};
+    EvalPlan P{};
+    P.mode = kModeHT;
+    P.nsets = nsets;
+    P.D = D;
+    P.tile_dirs = tdh;
+    P.chunk_req = t->tuning.chunk;
+    P.target_items = target;
+    P.npairs = npairs;
+    P.max_items = max_items;
+    P.dirs = d_dirs;
+    P.ctl = cv.take<int>(4);
+    P.perm = cv.take<int>((size_t)nsets * D);
+    P.rank = cv.take<int>((size_t)nsets * D);
+    P.boff = cv.take<int>((size_t)nsets * (NO + 1));
+    P.pair_items = cv.take<long long>(npairs + 1);
+    P.pair_chunks = cv.take<int>(npairs);
+    P.thr = nullptr;
+    P.T = 0;
+    double* part = cv.take<double>(part_elems);
+
+    TOPOT_CUDA(launch_dir_prep(P, t->n, st));
+    TOPOT_CUDA(launch_plan(P, t->dev(), st));
+    const int per_sm = t->tuning.ctas_per_sm > 0 ? t->tuning.ctas_per_sm : 4;
+    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, false, dl, t->sm_count * per_sm, part, st));
+    TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, d_out, st));
+    return TOPOT_OK;
+}
+
+}  // extern "C"
