@@ -76,13 +76,15 @@ typedef enum { TOPOT_FP32C = 0, TOPOT_FP64 = 1 } topot_precision;
 
 typedef struct topot_tables topot_tables;   /* opaque; owns the device tables */
 
-/* Tile shapes of the evaluation kernels; 0 = library default.  Set by the
- * autotuner of the Python binding, or by hand. */
+/* Tile shapes of the evaluation kernels, per operation; 0 = library default.  Set by
+ * the autotuner of the Python binding, or by hand. */
 typedef struct {
-    int ect_dirs_per_warp;    /* 8, 16 or 32 directions share one warp (ECT, Radon)  */
-    int ht_dirs_per_lane;     /* 1, 2 or 4 directions per lane (hybrid, FP32C)       */
-    int chunk;                /* critical points per work item (multiple of 256)     */
-    int ctas_per_sm;          /* resident blocks per SM of the persistent grids      */
+    int ect_dirs_per_warp;    /* ECT / Radon: 8, 16 or 32 directions share one warp       */
+    int ect_chunk;            /* ECT / Radon: critical points per work item (x256)        */
+    int ect_ctas_per_sm;      /* ECT / Radon: resident blocks per SM of the persistent grid */
+    int ht_dirs_per_lane;     /* hybrid FP32C: 1, 2, 4 (8: Laplace) directions per lane    */
+    int ht_chunk;             /* hybrid: critical points per work item (x256)             */
+    int ht_ctas_per_sm;       /* hybrid: resident blocks per SM of the persistent grid     */
 } topot_tuning;
 
 /* ---------------------------------------------------------------------------

@@ -37,8 +37,11 @@ class TopotError(RuntimeError):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("ect_dirs_per_warp", ctypes.c_int), ("ht_dirs_per_lane", ctypes.c_int),
-                ("chunk", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("ect_dirs_per_warp", ctypes.c_int), ("ect_chunk", ctypes.c_int), ("ect_ctas_per_sm", ctypes.c_int),
+                ("ht_dirs_per_lane", ctypes.c_int), ("ht_chunk", ctypes.c_int), ("ht_ctas_per_sm", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None
@@ -207,9 +210,16 @@ class Tables:
                                           val.ctypes.data_as(ctypes.c_void_p)))
         return idx[:cnt].astype(np.int64), val[:cnt].astype(np.int64)
 
-    def set_tuning(self, ect_dirs_per_warp=0, ht_dirs_per_lane=0, chunk=0, ctas_per_sm=0):
-        tu = Tuning(ect_dirs_per_warp, ht_dirs_per_lane, chunk, ctas_per_sm)
+    def set_tuning(self, **kw):
+        """Tile shapes per operation (fields of Tuning; omitted fields keep their value)."""
+        cur = getattr(self, "_tuning", Tuning())
+        tu = Tuning(**{**cur.as_dict(), **kw})
         _check(load().tables_set_tuning(self.handle, ctypes.byref(tu)))
+        self._tuning = tu
+
+    @property
+    def tuning(self) -> dict:
+        return getattr(self, "_tuning", Tuning()).as_dict()
 
 
 def build_critical_tables(batch: ImageBatch, stream=None) -> Tables:
@@ -290,3 +300,63 @@ class HybridTransform(torch.autograd.Function):
         (dirs,) = ctx.saved_tensors
         g = hybrid_transform_grad(ctx.tables, ctx.kernel, dirs.detach(), gout, ctx.precision)
         return g, None, None, None
+
+
+class Pipeline:
+    """Extraction + ECT (+ Radon) + hybrid transforms of a fixed batch layout, replayed as
+    one CUDA graph.
+
+    The tables handle, the pixel buffer and every output are allocated once; ``run``
+    copies new pixels into the captured input buffer and replays the graph (no host
+    synchronisation, no allocation, every kernel of the path in one graph launch).
+    """
+
+    def __init__(self, shapes, offsets, n_pixels: int, dtype=U8, ect=None, radon=None, hybrid=(),
+                 device="cuda"):
+        """ect / radon: (dirs, t_min, t_max, T) or None; hybrid: list of (kernel, dirs, precision)."""
+        self.tables = tables_create(shapes, offsets, dtype)
+        tdt = torch.uint8 if dtype == U8 else torch.int32
+        self.pixels = torch.zeros(n_pixels, dtype=tdt, device=device)
+        self.ect_args, self.radon_args, self.hybrid_args = ect, radon, list(hybrid)
+        B = self.tables.B
+        self.ect_out = None if ect is None else torch.empty(
+            (B, ect[0].shape[-2], ect[3]), dtype=torch.int32, device=device)
+        self.radon_out = None if radon is None else torch.empty(
+            (B, radon[0].shape[-2], radon[3]), dtype=torch.int32, device=device)
+        self.hybrid_out = []
+        for kernel, dirs, _prec in self.hybrid_args:
+            D = dirs.shape[-2]
+            shape = (B, D, 2) if kernel == "fourier" else (B, D)
+            self.hybrid_out.append(torch.empty(shape, dtype=torch.float64, device=device))
+        self.graph = None
+
+    def _launch(self):
+        self.tables.build(self.pixels)
+        if self.ect_args is not None:
+            d, a, b, T = self.ect_args
+            ect(self.tables, d, a, b, T, out=self.ect_out)
+        if self.radon_args is not None:
+            d, a, b, T = self.radon_args
+            radon(self.tables, d, a, b, T, out=self.radon_out)
+        for (kernel, d, prec), out in zip(self.hybrid_args, self.hybrid_out):
+            hybrid_transform(self.tables, kernel, d, prec, out=out)
+
+    def capture(self):
+        """Run once eagerly (sizes every workspace), then capture the launch sequence."""
+        self._launch()
+        torch.cuda.synchronize()
+        self.tables.sync()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._launch()
+        torch.cuda.synchronize()
+        return self
+
+    def run(self, pixels=None):
+        if pixels is not None:
+            self.pixels.copy_(pixels, non_blocking=True)
+        if self.graph is None:
+            self._launch()
+        else:
+            self.graph.replay()
+        return self

@@ -381,7 +381,8 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
     if ((u.ect_dirs_per_warp && u.ect_dirs_per_warp != 8 && u.ect_dirs_per_warp != 16 && u.ect_dirs_per_warp != 32) ||
         (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4 &&
          u.ht_dirs_per_lane != 8) ||
-        u.chunk < 0 || (u.chunk % 256) != 0 || u.ctas_per_sm < 0 || u.ctas_per_sm > 32)
+        u.ect_chunk < 0 || (u.ect_chunk % 256) != 0 || u.ht_chunk < 0 || (u.ht_chunk % 256) != 0 ||
+        u.ect_ctas_per_sm < 0 || u.ect_ctas_per_sm > 32 || u.ht_ctas_per_sm < 0 || u.ht_ctas_per_sm > 32)
         return fail(TOPOT_ERR_INVALID_ARG, "tables_set_tuning: value out of range");
     t->tuning = u;
     return TOPOT_OK;
@@ -430,7 +431,7 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     P.nsets = nsets;
     P.D = D;
     P.tile_dirs = td;
-    P.chunk_req = t->tuning.chunk;
+    P.chunk_req = t->tuning.ect_chunk;
     P.target_items = t->sm_count * 16;
     P.npairs = npairs;
     P.max_items = 1ll << 40;
@@ -453,7 +454,7 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
     int per_sm = std::max(1, (int)((220 * 1024) / (hist_smem_bytes(td, T) + 1024)));
     per_sm = std::min(per_sm, 8);
-    if (t->tuning.ctas_per_sm > 0) per_sm = std::min(per_sm, t->tuning.ctas_per_sm);
+    if (t->tuning.ect_ctas_per_sm > 0) per_sm = std::min(per_sm, t->tuning.ect_ctas_per_sm);
     TOPOT_CUDA(launch_hist(P, t->dev(), td, d_out, hi, t->sm_count * per_sm, st));
     TOPOT_CUDA(launch_hist_finish(mode, t->B, D, T, t->chi, d_out, hi, st));
     return TOPOT_OK;
@@ -501,10 +502,10 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     const int npairs = t->B * NO;
     const int target = t->sm_count * 16;
     long long max_items;
-    if (t->tuning.chunk > 0) {
+    if (t->tuning.ht_chunk > 0) {
         max_items = 0;
         for (int b = 0; b < t->B; ++b)
-            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.chunk - 1) / t->tuning.chunk);
+            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
     } else {
         max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
     }
@@ -520,7 +521,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     P.nsets = nsets;
     P.D = D;
     P.tile_dirs = tdh;
-    P.chunk_req = t->tuning.chunk;
+    P.chunk_req = t->tuning.ht_chunk;
     P.target_items = target;
     P.npairs = npairs;
     P.max_items = max_items;
@@ -537,7 +538,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
 
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
-    const int per_sm = t->tuning.ctas_per_sm > 0 ? t->tuning.ctas_per_sm : 4;
+    const int per_sm = t->tuning.ht_ctas_per_sm > 0 ? t->tuning.ht_ctas_per_sm : 4;
     TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, adjoint, dl, t->sm_count * per_sm, part, st));
     if (adjoint)
         TOPOT_CUDA(launch_ht_adj_combine(P, t->n, t->B, kernel, precision, tdh, part, d_gout, d_out, st));
@@ -640,10 +641,10 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
     const int npairs = t->B * NO;
     const int target = t->sm_count * 16;
     long long max_items;
-    if (t->tuning.chunk > 0) {
+    if (t->tuning.ht_chunk > 0) {
         max_items = 0;
         for (int b = 0; b < t->B; ++b)
-            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.chunk - 1) / t->tuning.chunk);
+            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
     } else {
         max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
     }
@@ -667,7 +668,7 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
     P.nsets = nsets;
     P.D = D;
     P.tile_dirs = tdh;
-    P.chunk_req = t->tuning.chunk;
+    P.chunk_req = t->tuning.ht_chunk;
     P.target_items = target;
     P.npairs = npairs;
     P.max_items = max_items;
@@ -684,7 +685,7 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
 
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
-    const int per_sm = t->tuning.ctas_per_sm > 0 ? t->tuning.ctas_per_sm : 4;
+    const int per_sm = t->tuning.ht_ctas_per_sm > 0 ? t->tuning.ht_ctas_per_sm : 4;
     TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, false, dl, t->sm_count * per_sm, part, st));
     TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, d_out, st));
     return TOPOT_OK;

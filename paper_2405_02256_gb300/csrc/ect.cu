@@ -281,19 +281,24 @@ __global__ void k_hist_finish(int mode, int B, int D, int T, const long long* ch
     }
 }
 
+// Kernel attributes are set once per instantiation (largest dynamic shared memory, max
+// shared carveout), so that later launches -- also inside stream capture -- only launch.
+static cudaError_t set_smem_attrs(const void* k) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <int NDIM, typename Tval>
 static cudaError_t launch_hist_n(const EvalPlan& P, const TablesDev& t, int td, int32_t* lo, int32_t* hi,
                                  int grid, cudaStream_t st) {
     const size_t smem = sizeof(float4) * kHistSub + sizeof(int) * (size_t)td * (P.T + 1);
-    cudaError_t e;
 #define TOPOT_HIST_CASE(TDV)                                                                   \
     case TDV: {                                                                                \
         auto k = k_hist<NDIM, TDV, Tval>;                                                      \
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        if (e == cudaSuccess)                                                                  \
-            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,        \
-                                     cudaSharedmemCarveoutMaxShared);                          \
-        if (e != cudaSuccess) return e;                                                        \
+        static cudaError_t attr = set_smem_attrs(reinterpret_cast<const void*>(k));            \
+        if (attr != cudaSuccess) return attr;                                                  \
         k<<<grid, kHistBlock, smem, st>>>(P, t, lo, hi);                                       \
         break;                                                                                 \
     }

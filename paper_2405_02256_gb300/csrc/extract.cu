@@ -318,10 +318,15 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
 template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
 static cudaError_t launch_extract_t(const ExtractArgs& a, size_t smem, cudaStream_t st) {
     auto kern = k_extract<NDIM, Tin, Tval, BLOCK, K>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
+    // attributes once per instantiation, so that launches inside stream capture only launch
+    static cudaError_t attr = [&] {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        return e;
+    }();
+    if (attr != cudaSuccess) return attr;
     kern<<<(unsigned)a.num_tiles, BLOCK, smem, st>>>(a);
     return cudaGetLastError();
 }
