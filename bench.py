@@ -246,28 +246,32 @@ def run_gpu(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    # issue-slot peak of the FP32 / MUFU path: 4 schedulers x 32 lanes per SM per clock
+    # FP32 pipe: 128 lanes per SM per clock; issue: 4 schedulers x 32 lanes per SM per clock
     lane_ops = sm_count * 128 * mhz * 1e6
-    # minimal instructions per term (FP32 pipe + MUFU), see the design doc
-    slots = {"ht_laplace": 7.0, "ht_fourier": 12.0, "ht_bessel": 17.0}
-    mufu = {"ht_laplace": 1.0, "ht_fourier": 2.0, "ht_bessel": 0.0}
+    # FP32-pipe lane operations per term of each hybrid kernel as written (a packed f32x2
+    # operation counts 2, MUFU operations are not counted), and issued instructions per
+    # (point, direction) update of the ECT kernel; both counted from the source, see the design doc
+    fp32_ops = {"ht_laplace": 3.5, "ht_fourier": 9.5, "ht_bessel": 7.5}
+    ect_instr = 16.0
     if names[dom] == "extract":
         achieved = ext_bytes / (ph_ms[dom] / 1e3) / 1e9
         roof = {"kernel": "k_extract", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": "measured hbm_gbs"}
+                "frac": achieved / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS hbm_gbs (of measured)"}
     elif names[dom] == "ect":
-        per_upd = 12.0
-        achieved = ect_updates * per_upd / (ph_ms[dom] / 1e3) / 1e12
-        peak = lane_ops / 1e12
-        roof = {"kernel": "k_hist", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-ops/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "152 SM x 128 lanes x max clock"}
+        achieved = ect_updates * ect_instr / 32 / (ph_ms[dom] / 1e3) / 1e12
+        peak = lane_ops / 32 / 1e12
+        roof = {"kernel": "k_hist", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Twarp-instr/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 4 issue slots x max SM clock (recipe unit counts)"}
     else:
         nm = names[dom]
         term_rate = terms / (ph_ms[dom] / 1e3)
-        peak_terms = min(lane_ops / slots[nm], (sm_count * 16 * mhz * 1e6 / mufu[nm]) if mufu[nm] else 1e30)
-        roof = {"kernel": "k_ht_f32<" + nm[3:] + ">", "bound": "alu", "achieved": term_rate / 1e9,
-                "peak": peak_terms / 1e9, "unit": "Gterms/s", "frac": term_rate / peak_terms, "traffic": None,
-                "peak_source": "issue slots (128 lanes/clk/SM) and MUFU (16/clk/SM) at max SM clock"}
+        achieved = term_rate * fp32_ops[nm] / 1e12
+        peak = lane_ops / 1e12
+        roof = {"kernel": "k_ht_f32<" + nm[3:] + ">", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tlane-ops/s (FP32 pipe)", "frac": achieved / peak, "traffic": None,
+                "terms_per_s": term_rate, "fp32_lane_ops_per_term": fp32_ops[nm],
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (recipe unit counts)"}
 
     launches_per_step = 1 + 4 + 4 * len(KERNELS)
     out = {
@@ -295,12 +299,158 @@ def run_gpu(args):
         "clocks": clocks,
         "setup_s": setup_s,
     }
+    if not args.no_extra:
+        out["rows"] = extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev)
+        tabs.free()
+        del batch
+        torch.cuda.empty_cache()
+        out["rows"].update(extra_workloads(dev))
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(imgs[0], dirs_ht_h, budget_s=args.cpu_budget)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _time_cuda(fn, reps: int = 3) -> float:
+    """Mean ms of fn over reps launches, after one warm-up (CUDA events, current stream)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _orthants(dirs: np.ndarray) -> np.ndarray:
+    n = dirs.shape[1]
+    return sum(((dirs[:, k] < 0).astype(np.int64) << k) for k in range(n))
+
+
+def _sizes(tabs, n_img, NO):
+    nl = np.array([[tabs.info(b, o)[0] for o in range(NO)] for b in range(n_img)], dtype=np.int64)
+    nd = np.array([[tabs.info(b, o)[1] for o in range(NO)] for b in range(n_img)], dtype=np.int64)
+    return nl, nd
+
+
+def extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev):
+    """Every other row of the hot path, measured on its own workload."""
+    import torch
+
+    from paper_2405_02256_gb300 import binding as tb
+    from paper_2405_02256_gb300 import synth
+    rows = {}
+    R2 = synth.image_radius(2)
+
+    # a6: Radon on the same 2048^2 tables, 1024 directions x 512 thresholds (two tables per direction)
+    out = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
+    ms = _time_cuda(lambda: tb.radon(tabs, dirs_ect, -R2, R2, T_ECT, out=out))
+    cnt = np.bincount(_orthants(dirs_ect_h), minlength=4)
+    upd = int(sum(cnt[o] * (nl[:, o] + nl[:, o ^ 3]).sum() for o in range(4)))
+    rows["radon_2d"] = {"workload": "same 64 x 2048^2 tables; 1024 dirs x 512 thresholds", "ms": ms,
+                        "dirs_per_s": n_img * D_ECT / (ms / 1e3), "updates_per_s": upd / (ms / 1e3)}
+
+    # a8: adjoint of Laplace and Fourier at the 4096 hybrid directions
+    terms = int((nd * np.bincount(_orthants(dirs_ht_h), minlength=4)[None, :]).sum())
+    g = torch.empty_like(dirs_ht)
+    adj = {}
+    for k in ("laplace", "fourier"):
+        gout = torch.ones((n_img, D_HT, 2) if k == "fourier" else (n_img, D_HT), dtype=torch.float64, device=dev)
+        ms = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, dirs_ht, gout, "fp32c", out=g), reps=1)
+        adj[k] = {"ms": ms, "terms_per_s": terms / (ms / 1e3)}
+    rows["adjoint_2d"] = {"workload": "same tables; 4096 dirs, d/dxi of sum_b,d HT", **adj}
+    return rows
+
+
+def extra_workloads(dev):
+    """BASELINE configurations 3-5: 3-D volumes, ragged batch under a CUDA graph, gradients."""
+    import torch
+
+    from paper_2405_02256_gb300 import binding as tb
+    from paper_2405_02256_gb300 import synth
+    rows = {}
+
+    # configuration 4: 10,000 ragged grey images, one CUDA graph per step
+    t0 = time.time()
+    shapes = synth.ragged_shapes(10000, 28, 512, seed=4)
+    imgs = [synth.blurred_noise(s, 2.0, seed=400000 + i) for i, s in enumerate(shapes)]
+    gen_s = time.time() - t0
+    batch = tb.pack_images(imgs, device=dev)
+    R2 = synth.image_radius(2)
+    ect_h = synth.circle_dirs(64)
+    ht_h = synth.random_2d_dirs(256, 44, 1.0, 1.0)
+    pipe = tb.Pipeline(batch.shapes, batch.offsets, batch.pixels.numel(),
+                       ect=(torch.from_numpy(ect_h).to(dev), -R2, R2, 64),
+                       hybrid=[("laplace", torch.from_numpy(ht_h).to(dev), "fp32c")])
+    pipe.pixels.copy_(batch.pixels)
+    pipe.capture()
+    ms = _time_cuda(lambda: pipe.run(), reps=5)
+    nl, nd = _sizes(pipe.tables, len(imgs), 4)
+    terms = int((nd * np.bincount(_orthants(ht_h), minlength=4)[None, :]).sum())
+    px = int(batch.pixels.numel())
+    rows["ragged_graph_2d"] = {
+        "workload": "10,000 grey images, sides log-uniform in [28, 512], blurred noise sigma 2; ECT 64 x 64 and "
+                    "Laplace at 256 unit dirs per image; extraction + ECT + Laplace replayed as one CUDA graph",
+        "ms_per_step": ms, "images_per_s": len(imgs) / (ms / 1e3), "pixels": px,
+        "ect_dirs_per_s": len(imgs) * 64 / (ms / 1e3), "laplace_terms_per_s_whole_step": terms / (ms / 1e3),
+        "input_gen_s": gen_s}
+    pipe.tables.free()
+    del pipe, batch, imgs
+
+    # configuration 3: 4 binary volumes 256^3, ECT / Radon at 2048 Fibonacci dirs x 256, Fourier at 8192
+    vols = [synth.grf((256, 256, 256), 8.0, seed=300 + b, binary=True) for b in range(4)]
+    batch = tb.pack_images(vols, device=dev)
+    R3 = synth.image_radius(3)
+    fib = synth.fibonacci_dirs(2048)
+    four = synth.scale_norms(synth.fibonacci_dirs(8192), 3, 0.05, 2.0)
+    tabs = tb.tables_create(batch.shapes, batch.offsets)
+    ms_ext = _time_cuda(lambda: tabs.build(batch.pixels))
+    tabs.sync()
+    nl, nd = _sizes(tabs, 4, 8)
+    ent = int(nl.sum() + nd[:, :4].sum())
+    d_f = torch.from_numpy(fib).to(dev)
+    d_4 = torch.from_numpy(four).to(dev)
+    out = torch.empty((4, 2048, 256), dtype=torch.int32, device=dev)
+    ms_ect = _time_cuda(lambda: tb.ect(tabs, d_f, -R3, R3, 256, out=out))
+    ms_rad = _time_cuda(lambda: tb.radon(tabs, d_f, -R3, R3, 256, out=out))
+    o4 = torch.empty((4, 8192, 2), dtype=torch.float64, device=dev)
+    ms_f = _time_cuda(lambda: tb.hybrid_transform(tabs, "fourier", d_4, "fp32c", out=o4))
+    terms = int((nd * np.bincount(_orthants(four), minlength=8)[None, :]).sum())
+    rows["volumes_3d"] = {
+        "workload": "4 binary GRF volumes 256^3 (ell=8); ECT and Radon at 2048 Fibonacci dirs x 256; "
+                    "Fourier at 8192 dirs, |xi| uniform [0.05, 2]",
+        "extract_ms": ms_ext, "extract_gbs": (batch.pixels.numel() + 6 * ent) / (ms_ext / 1e3) / 1e9,
+        "ect_ms": ms_ect, "ect_dirs_per_s": 4 * 2048 / (ms_ect / 1e3),
+        "radon_ms": ms_rad, "radon_dirs_per_s": 4 * 2048 / (ms_rad / 1e3),
+        "fourier_ms": ms_f, "fourier_terms_per_s": terms / (ms_f / 1e3)}
+    tabs.free()
+    del batch, vols
+
+    # configuration 5: one 128^3 grey volume, Laplace and Fourier forward + adjoint at 8192 dirs
+    vol = synth.grf((128, 128, 128), 6.0, seed=5)
+    batch = tb.pack_images([vol], device=dev)
+    tabs = tb.build_critical_tables(batch)
+    xi = synth.sphere_dirs(8192, 6, 0.1, 1.0)
+    d = torch.from_numpy(xi).to(dev)
+    nl, nd = _sizes(tabs, 1, 8)
+    terms = int((nd * np.bincount(_orthants(xi), minlength=8)[None, :]).sum())
+    res = {}
+    for k in ("laplace", "fourier"):
+        o = torch.empty((1, 8192, 2) if k == "fourier" else (1, 8192), dtype=torch.float64, device=dev)
+        ms_fw = _time_cuda(lambda: tb.hybrid_transform(tabs, k, d, "fp32c", out=o))
+        g = torch.empty_like(d)
+        gout = torch.ones_like(o)
+        ms_bw = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, d, gout, "fp32c", out=g))
+        res[k] = {"forward_ms": ms_fw, "adjoint_ms": ms_bw, "forward_terms_per_s": terms / (ms_fw / 1e3),
+                  "adjoint_terms_per_s": terms / (ms_bw / 1e3)}
+    rows["gradients_3d"] = {"workload": "128^3 grey GRF (ell=6); 8192 dirs, |xi| in [0.1, 1]", **res}
+    tabs.free()
+    return rows
 
 
 def cpu_baseline(img, dirs_ht, budget_s: float = 20.0):
@@ -365,6 +515,7 @@ def main():
     p.add_argument("--side", type=int, default=SIDE)
     p.add_argument("--cpu-budget", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the other rows and configurations")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)
