@@ -390,6 +390,7 @@ def extra_workloads(dev):
     pipe.pixels.copy_(batch.pixels)
     pipe.capture()
     ms = _time_cuda(lambda: pipe.run(), reps=5)
+    pipe.tables.sync()
     nl, nd = _sizes(pipe.tables, len(imgs), 4)
     terms = int((nd * np.bincount(_orthants(ht_h), minlength=4)[None, :]).sum())
     px = int(batch.pixels.numel())

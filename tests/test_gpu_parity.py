@@ -284,3 +284,24 @@ def test_rebuild_async_and_deterministic(tb):
     assert torch.equal(h1, h2)
     tabs.sync()
     _check_tables(tabs, 0, imgs[0])
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+def test_gradient_3d(tb, kernel):
+    img = synth.grf((18, 21, 24), 3.0, seed=65)
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    dirs = synth.sphere_dirs(160, 66, 0.1, 1.0)
+    rng = np.random.default_rng(67)
+    nc = 2 if kernel == "fourier" else 1
+    gout = rng.standard_normal((1, 160, 2)) if nc == 2 else rng.standard_normal((1, 160))
+    got = tb.hybrid_transform_grad(tabs, kernel, torch.from_numpy(dirs).cuda(),
+                                   torch.from_numpy(gout).cuda()).cpu().numpy()
+    g, gn = O.hybrid_transform_grad(ref, kernel, dirs)
+    if kernel == "fourier":
+        want = gout[0, :, 0:1] * g.real + gout[0, :, 1:2] * g.imag
+        sc = (np.abs(gout[0, :, 0:1]) + np.abs(gout[0, :, 1:2])) * gn
+    else:
+        want = gout[0][:, None] * g
+        sc = np.abs(gout[0])[:, None] * gn
+    assert np.max(np.abs(got - want) / sc) <= 2e-6
