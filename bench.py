@@ -98,6 +98,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """Job time: the maximum over ranks (a no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks over the job time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def _dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -183,15 +199,11 @@ def run_gpu(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    total_ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(stop), dev)
     ms_step = total_ms / args.steps
     ph = np.array([[evs[s][i].elapsed_time(evs[s][i + 1]) for i in range(5)] for s in range(args.steps)])
     ph_ms = ph.mean(axis=0)
-    value = terms * 3 * world / (ms_step / 1e3)
+    value = whole_job_rate(terms * 3, world, ms_step)
 
     # ---- plain FP64 hybrid path on a direction sample ---------------------------------------
     sample = dirs_ht[:FP64_SAMPLE_DIRS].contiguous()
