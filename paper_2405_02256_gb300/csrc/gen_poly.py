@@ -7,6 +7,7 @@ exact rational arithmetic, so no library routine enters the constants:
 
 * J0(2 sqrt(y)) = sum_k (-y)^k / (k!)^2            (Abramowitz & Stegun 9.1.10)
 * cos(sqrt(w))  = sum_k (-w)^k / (2k)!
+* sin(sqrt(w)) / sqrt(w) = sum_k (-w)^k / (2k+1)!   (sin z = z q(z^2))
 
 The script prints the FP32 constants (copied into ht.cu) and the worst absolute error of
 an FP32 Horner evaluation with fused multiply-adds on a fine grid.
@@ -23,7 +24,7 @@ def series(kind: str, x: Fraction, terms: int = 40) -> Fraction:
     s = Fraction(0)
     p = Fraction(1)
     for k in range(terms):
-        den = factorial(k) ** 2 if kind == "j0" else factorial(2 * k)
+        den = {"j0": factorial(k) ** 2, "cos": factorial(2 * k), "sinc": factorial(2 * k + 1)}[kind]
         s += p / den
         p *= -x
     return s
@@ -62,3 +63,5 @@ if __name__ == "__main__":
     report("j0", 1.0, 5)        # |z| <= 2
     report("cos", 0.5625, 3)    # |z| <= 0.75
     report("cos", 3.0625, 5)    # |z| <= 1.75
+    report("sinc", 0.5625, 3)   # |z| <= 0.75
+    report("sinc", 3.0625, 5)   # |z| <= 1.75

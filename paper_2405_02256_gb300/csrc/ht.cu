@@ -224,6 +224,18 @@ __device__ __forceinline__ float2 cos_long2(float2 w) {
     return horner2(c, w);
 }
 
+// sin z = z q(z^2): X = 0.5625 (|z| <= 0.75), d = 3, 4e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
+__device__ __forceinline__ float2 sinc_short2(float2 w) {
+    constexpr float c[4] = {1.000000000e+00f, -1.666665524e-01f, 8.332253434e-03f, -1.953341998e-04f};
+    return horner2(c, w);
+}
+
+__device__ __forceinline__ float2 sinc_long2(float2 w) {
+    constexpr float c[6] = {1.000000000e+00f, -1.666666716e-01f, 8.333328180e-03f, -1.984049450e-04f,
+                            2.750829026e-06f, -2.361634976e-08f};
+    return horner2(c, w);
+}
+
 __device__ __forceinline__ float2 j0_short2(float2 y) {
     constexpr float c[4] = {9.999999404e-01f, -9.999933243e-01f, 2.498667836e-01f, -2.692156099e-02f};
     return horner2(c, y);
@@ -245,16 +257,22 @@ __device__ __forceinline__ void kahan2_add(float2& s, float2& nc, float2 x) {
     s = t;
 }
 
-// Fourier: sin always on the MUFU pipe; cos on the MUFU pipe for odd pairs and as a
-// polynomial on the FMA pipe for even pairs, which balances the two pipes.
+// Fourier: odd pairs take sin and cos from the MUFU pipe, even pairs evaluate both as
+// polynomials in w = z^2 on the FMA pipe; half and half keeps both pipes busy (a MUFU
+// sin/cos costs two XU cycles, the polynomial pair about 9 FP32 operations).
 template <int KERNEL, int PATH>
 __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_cos) {
     if (KERNEL == TOPOT_LAPLACE) {
         k[0] = make_float2(ex2_approx(z.x), ex2_approx(z.y));
     } else if (KERNEL == TOPOT_FOURIER) {
-        k[0] = make_float2(__sinf(z.x), __sinf(z.y));
-        if (mufu_cos) k[1] = make_float2(__cosf(z.x), __cosf(z.y));
-        else k[1] = PATH == 2 ? cos_short2(mul2(z, z)) : cos_long2(mul2(z, z));
+        if (mufu_cos) {
+            k[0] = make_float2(__sinf(z.x), __sinf(z.y));
+            k[1] = make_float2(__cosf(z.x), __cosf(z.y));
+        } else {
+            const float2 w = mul2(z, z);
+            k[0] = mul2(z, PATH == 2 ? sinc_short2(w) : sinc_long2(w));
+            k[1] = PATH == 2 ? cos_short2(w) : cos_long2(w);
+        }
     } else {
         const float2 y = mul2(z, z);   // z is already halved
         k[0] = PATH == 2 ? j0_short2(y) : j0_long2(y);
