@@ -130,9 +130,15 @@ __device__ __forceinline__ HtItem ht_item(const EvalPlan& P, const TablesDev& t,
 // X = (x0, x1, x2) embedding coordinates (adjoint only).
 template <int NDIM, int KERNEL, bool WITH_X, typename Tval, bool PACKED = false>
 __device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, long long e0, int cnt,
-                                         float4* A, float4* X) {
+                                         float4* A, float4* X, int cnt_pad = 0) {
     const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
     const ImgDesc& I = *it.I;
+    if (PACKED) {   // zero-value points after the last one, up to cnt_pad
+        for (int i = cnt + threadIdx.x; i < cnt_pad; i += kHtBlock) {
+            A[2 * i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            A[2 * i + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
     for (int i = threadIdx.x; i < cnt; i += kHtBlock) {
         const uint32_t idx = (uint32_t)t.arena_idx[it.base + e0 + i];
         const float v = (float)aval[it.base + e0 + i];
@@ -289,33 +295,37 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
                                                 float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr int BLK = KERNEL == TOPOT_FOURIER ? 4 : 8;
-    int e = ws;
-    for (; e < we; e += BLK) {
-        const int nb = min(BLK, we - e);
-        float2 blk[NPR][NC];
+    // [ws, we) is a multiple of BLK long (rounds are padded with zero-value points); each
+    // block is summed in two interleaved chains (even / odd points) to halve the
+    // dependency depth, then added with compensation.
+    for (int e = ws; e < we; e += BLK) {
+        float2 ba[NPR][NC], bb[NPR][NC];
 #pragma unroll
         for (int u = 0; u < BLK; ++u) {
-            if (u < nb) {
-                const float4 qa = A[2 * (e + u)];
-                const float4 qb = A[2 * (e + u) + 1];
-                const float2 c0 = make_float2(qa.x, qa.y), c1 = make_float2(qa.z, qa.w);
-                const float2 c2 = make_float2(qb.x, qb.y), v2 = make_float2(qb.z, qb.w);
+            const float4 qa = A[2 * (e + u)];
+            const float4 qb = A[2 * (e + u) + 1];
+            const float2 c0 = make_float2(qa.x, qa.y), c1 = make_float2(qa.z, qa.w);
+            const float2 c2 = make_float2(qb.x, qb.y), v2 = make_float2(qb.z, qb.w);
 #pragma unroll
-                for (int pq = 0; pq < NPR; ++pq) {
-                    float2 z = mul2(c0, w[pq][0]);
-                    z = fma2(c1, w[pq][1], z);
-                    if (NDIM == 3) z = fma2(c2, w[pq][2], z);
-                    float2 k[2];
-                    kernel_pair<KERNEL, PATH>(z, k, (pq & 1) == 1);
+            for (int pq = 0; pq < NPR; ++pq) {
+                float2 z = mul2(c0, w[pq][0]);
+                z = fma2(c1, w[pq][1], z);
+                if (NDIM == 3) z = fma2(c2, w[pq][2], z);
+                float2 k[2];
+                kernel_pair<KERNEL, PATH>(z, k, (pq & 1) == 1);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) blk[pq][c] = u == 0 ? mul2(v2, k[c]) : fma2(v2, k[c], blk[pq][c]);
+                for (int c = 0; c < NC; ++c) {
+                    if (u == 0) ba[pq][c] = mul2(v2, k[c]);
+                    else if (u == 1) bb[pq][c] = mul2(v2, k[c]);
+                    else if (u & 1) bb[pq][c] = fma2(v2, k[c], bb[pq][c]);
+                    else ba[pq][c] = fma2(v2, k[c], ba[pq][c]);
                 }
             }
         }
 #pragma unroll
         for (int pq = 0; pq < NPR; ++pq)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) kahan2_add(s2[pq][c], n2[pq][c], blk[pq][c]);
+            for (int c = 0; c < NC; ++c) kahan2_add(s2[pq][c], n2[pq][c], add2(ba[pq][c], bb[pq][c]));
     }
 }
 
@@ -419,10 +429,12 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
                 const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
                 __syncthreads();
-                ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr);
+                // pad the round to 8 points per warp per block with zero-value points
+                const int cnt_pad = (cnt + kHtWarps * 8 - 1) / (kHtWarps * 8) * (kHtWarps * 8);
+                ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr, cnt_pad);
                 __syncthreads();
-                const int per = (cnt + kHtWarps - 1) / kHtWarps;
-                const int ws = warp * per, we = min(cnt, ws + per);
+                const int per = cnt_pad / kHtWarps;
+                const int ws = warp * per, we = ws + per;
                 if (path == 2) ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2);
                 else ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2);
             }
