@@ -408,9 +408,10 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     if (T < 2 || !(t_max > t_min) || !std::isfinite(t_min) || !std::isfinite(t_max))
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": need T >= 2 and finite t_min < t_max");
     if (t->host_valid) {
+        const long long lim = mode == kModeRadon ? (1ll << 31) / 3 : (1ll << 31);
         for (long long v : t->h_absum)
-            if (v >= (1ll << 31))
-                return fail(TOPOT_ERR_OVERFLOW, std::string(name) + ": sum |Delta^-| >= 2^31 overflows int32");
+            if (v >= lim)
+                return fail(TOPOT_ERR_OVERFLOW, std::string(name) + ": sum |Delta^-| too large for int32 results");
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int nsets = per_image_dirs ? t->B : 1;

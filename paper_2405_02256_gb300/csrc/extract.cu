@@ -75,7 +75,7 @@ __device__ __forceinline__ void lower_star(const Tin* c, int rs, int ps, int (&o
 }
 
 template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
-__global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
+__global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     using PT = PixTraits<Tin>;
     constexpr int NO = 1 << NDIM;              // orthants
     constexpr int S = NO + NO / 2;             // segments
@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
 
     const long long ticket = sh_int[0];
     const int b = sh_int[1];
-    const ImgDesc& I = T.img[b];
+    // a register copy: the table stores below could alias a reference into global memory
+    const ImgDesc I = T.img[b];
     const int m0 = I.m[0], m1 = I.m[1], m2 = I.m[2];
     const long long lt = ticket - I.tile_begin;
     const long long ntiles_img = (long long)I.tiles_per_plane * m2;
@@ -187,31 +188,42 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
     __syncthreads();
 
     // ---- 2. lower-star values, kept in registers --------------------------------------
+    // Vertex j of the tile (j = k * BLOCK + tid) has linear index L0 + j: the tile is a run
+    // of full rows (cols == m0) or part of one row.  Its staged position is tracked as
+    // (r, c) incrementally instead of dividing by the row length.
     int vals[K][NO];
-    int chi_acc = 0;          // |Delta^-| <= 2^n * 2^26 per vertex: K vertices fit int32 for u8,
-    int abs_acc[NO];          // and int32 input is limited to |phi| < 2^26 (checked below)
+    int chi_acc = 0;          // |Delta^-| <= 2^(n-1) * 255 per vertex for u8, and int32 input
+    int abs_acc[NO];          // is limited to |phi| < 2^26 (checked below): K vertices fit int32
 #pragma unroll
     for (int o = 0; o < NO; ++o) abs_acc[o] = 0;
     bool bad_pixel = false;
     const Tin* center0 = stage + (NP == 3 ? PS : 0) + RS + PAD;
+    {
+        const int W = cols;
+        int r = 0, c = tid;
+        if (rows > 1) { r = (int)fastdiv((uint32_t)tid, I.div0); c = tid - r * W; }
+        const int dq = rows > 1 ? BLOCK / W : 0;
+        const int dr = BLOCK - dq * W;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int j = k * BLOCK + tid;
-        if (j < nverts) {
-            int r = 0, c = j;
-            if (rows > 1) { r = (int)fastdiv((uint32_t)j, I.div0); c = j - r * m0; }
-            const Tin* cp = center0 + r * RS + c;
-            lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
-            if constexpr (PT::kSigned) {
-                const int a = (int)cp[0];
-                bad_pixel |= (a >= (1 << 26)) || (a <= -(1 << 26));
+        for (int k = 0; k < K; ++k) {
+            const int j = k * BLOCK + tid;
+            if (j < nverts) {
+                const Tin* cp = center0 + r * RS + c;
+                lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
+                if constexpr (PT::kSigned) {
+                    const int a = (int)cp[0];
+                    bad_pixel |= (a >= (1 << 26)) || (a <= -(1 << 26));
+                }
+                chi_acc += vals[k][0];
+#pragma unroll
+                for (int o = 0; o < NO; ++o) abs_acc[o] += abs(vals[k][o]);
+            } else {
+#pragma unroll
+                for (int o = 0; o < NO; ++o) vals[k][o] = 0;
             }
-            chi_acc += vals[k][0];
-#pragma unroll
-            for (int o = 0; o < NO; ++o) abs_acc[o] += abs(vals[k][o]);
-        } else {
-#pragma unroll
-            for (int o = 0; o < NO; ++o) vals[k][o] = 0;
+            c += dr;
+            r += dq;
+            if (c >= W) { c -= W; ++r; }
         }
     }
     if (bad_pixel) dev_set_error(T.err, kDevErrOverflow);
@@ -222,9 +234,9 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
 
     // ---- 3a. per-warp counts ------------------------------------------------------------
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int s = 0; s < S; ++s) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
+        for (int k = 0; k < K; ++k) {
             const unsigned bal = __ballot_sync(0xffffffffu, seg_value(k, s) != 0);
             if (lane == 0) sh_cnt[(s * K + k) * NW + warp] = __popc(bal);
         }
@@ -279,7 +291,8 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
             }
             st_relaxed_u64(st, kFlagP | ((unsigned long long)prefix + agg));
         }
-        sh_pref[s] = prefix;
+        // arena position of this tile's first entry of segment s
+        sh_pref[s] = I.seg_base + (long long)s * I.N + prefix;
         if (lt == ntiles_img - 1) T.seg_count[(long long)b * S + s] = prefix + (long long)agg;
     }
     if (tid == 0) {
@@ -290,24 +303,22 @@ __global__ void __launch_bounds__(BLOCK, 2) k_extract(ExtractArgs p) {
     }
     __syncthreads();
 
-    // ---- 3c. scatter the compacted entries --------------------------------------------
-    Tval* aval = reinterpret_cast<Tval*>(T.arena_val);
+    // ---- 3c. scatter the compacted entries, one segment at a time -----------------------
     const unsigned lt_mask = lanemask_lt();
+    const int vbase = (int)L0 + tid;          // linear index of vertex k = 0 (N < 2^31)
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int j = k * BLOCK + tid;
-        int r = 0, c = j;
-        if (rows > 1) { r = (int)fastdiv((uint32_t)(j < nverts ? j : 0), I.div0); c = j - r * m0; }
-        const int vidx = (int)(L0 + (long long)r * m0 + c);
+    for (int s = 0; s < S; ++s) {
+        int* __restrict__ didx = T.arena_idx + sh_pref[s];
+        Tval* __restrict__ dval = reinterpret_cast<Tval*>(T.arena_val) + sh_pref[s];
+        const int* cnt_s = sh_cnt + s * K * NW + warp;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
+        for (int k = 0; k < K; ++k) {
             const int v = seg_value(k, s);
             const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
             if (v != 0) {
-                const long long pos = I.seg_base + (long long)s * I.N + sh_pref[s] +
-                                      sh_cnt[(s * K + k) * NW + warp] + __popc(bal & lt_mask);
-                T.arena_idx[pos] = vidx;
-                aval[pos] = (Tval)v;
+                const int pos = cnt_s[k * NW] + __popc(bal & lt_mask);
+                didx[pos] = vbase + k * BLOCK;
+                dval[pos] = (Tval)v;
             }
         }
     }
@@ -332,7 +343,7 @@ static cudaError_t launch_extract_t(const ExtractArgs& a, size_t smem, cudaStrea
 }
 
 // Tile geometry shared with the host code: vertices per tile and block size.
-int extract_block(int n) { return n == 2 ? 512 : 512; }
+int extract_block(int n) { return n == 2 ? 256 : 256; }
 int extract_k(int n) { return n == 2 ? 8 : 4; }
 
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows) {
@@ -347,11 +358,11 @@ size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows)
 cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st) {
     const size_t smem = extract_smem_bytes(n, dtype == TOPOT_U8 ? 1 : 4, a.row_stride, a.stage_rows);
     if (n == 2) {
-        if (dtype == TOPOT_U8) return launch_extract_t<2, uint8_t, int16_t, 512, 8>(a, smem, st);
-        return launch_extract_t<2, int32_t, int32_t, 512, 8>(a, smem, st);
+        if (dtype == TOPOT_U8) return launch_extract_t<2, uint8_t, int16_t, 256, 8>(a, smem, st);
+        return launch_extract_t<2, int32_t, int32_t, 256, 8>(a, smem, st);
     }
-    if (dtype == TOPOT_U8) return launch_extract_t<3, uint8_t, int16_t, 512, 4>(a, smem, st);
-    return launch_extract_t<3, int32_t, int32_t, 512, 4>(a, smem, st);
+    if (dtype == TOPOT_U8) return launch_extract_t<3, uint8_t, int16_t, 256, 4>(a, smem, st);
+    return launch_extract_t<3, int32_t, int32_t, 256, 4>(a, smem, st);
 }
 
 }  // namespace topot

@@ -102,8 +102,11 @@ __global__ void __launch_bounds__(1024) k_plan(EvalPlan P, TablesDev t) {
         pair_info(p, tiles, N);
         work += (unsigned long long)(tiles * P.tile_dirs) * (unsigned long long)N;
     }
+    // int32 outputs: |ECT| <= sum_v |Delta^-_o|; |R| <= |ECT(xi)| + |ECT(-xi)| + |chi| <= 3 max_o of it
+    // (intermediate int32 sums may wrap: only the final values must fit)
+    const long long lim = P.mode == kModeRadon ? (1ll << 31) / 3 : (1ll << 31);
     for (int i = tid; i < t.B * NO; i += 1024)
-        if (P.mode != kModeHT && t.absum[i] >= (1ll << 31)) dev_set_error(t.err, kDevErrOverflow);
+        if (P.mode != kModeHT && t.absum[i] >= lim) dev_set_error(t.err, kDevErrOverflow);
     work = warp_sum(work);
     if (lane == 0) red[warp] = work;
     __syncthreads();
