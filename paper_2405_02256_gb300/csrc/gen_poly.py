@@ -8,6 +8,7 @@ exact rational arithmetic, so no library routine enters the constants:
 * J0(2 sqrt(y)) = sum_k (-y)^k / (k!)^2            (Abramowitz & Stegun 9.1.10)
 * cos(sqrt(w))  = sum_k (-w)^k / (2k)!
 * sin(sqrt(w)) / sqrt(w) = sum_k (-w)^k / (2k+1)!   (sin z = z q(z^2))
+* J1(2 sqrt(y)) / sqrt(y) = sum_k (-y)^k / (k! (k+1)!)  (A&S 9.1.10; J1(z) = (z/2) q((z/2)^2))
 
 The script prints the FP32 constants (copied into ht.cu) and the worst absolute error of
 an FP32 Horner evaluation with fused multiply-adds on a fine grid.
@@ -24,7 +25,8 @@ def series(kind: str, x: Fraction, terms: int = 40) -> Fraction:
     s = Fraction(0)
     p = Fraction(1)
     for k in range(terms):
-        den = {"j0": factorial(k) ** 2, "cos": factorial(2 * k), "sinc": factorial(2 * k + 1)}[kind]
+        den = {"j0": factorial(k) ** 2, "cos": factorial(2 * k), "sinc": factorial(2 * k + 1),
+               "j1q": factorial(k) * factorial(k + 1)}[kind]
         s += p / den
         p *= -x
     return s
@@ -65,3 +67,5 @@ if __name__ == "__main__":
     report("cos", 3.0625, 5)    # |z| <= 1.75
     report("sinc", 0.5625, 3)   # |z| <= 0.75
     report("sinc", 3.0625, 5)   # |z| <= 1.75
+    report("j1q", 0.25, 3)      # |z| <= 1
+    report("j1q", 1.0, 5)       # |z| <= 2

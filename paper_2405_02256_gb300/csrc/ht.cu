@@ -247,6 +247,18 @@ __device__ __forceinline__ float2 j0_short2(float2 y) {
     return horner2(c, y);
 }
 
+// J1(z) = (z/2) q((z/2)^2): X = 0.25 (|z| <= 1), d = 3, 6e-8;  X = 1 (|z| <= 2), d = 5, 6e-8
+__device__ __forceinline__ float2 j1q_short2(float2 y) {
+    constexpr float c[4] = {1.000000000e+00f, -4.999986589e-01f, 8.330661058e-02f, -6.772808731e-03f};
+    return horner2(c, y);
+}
+
+__device__ __forceinline__ float2 j1q_long2(float2 y) {
+    constexpr float c[6] = {1.000000000e+00f, -5.000000000e-01f, 8.333322406e-02f, -6.943985354e-03f,
+                            3.463324101e-04f, -1.077446268e-05f};
+    return horner2(c, y);
+}
+
 __device__ __forceinline__ float2 j0_long2(float2 y) {
     constexpr float c[6] = {1.000000000e+00f, -9.999999404e-01f, 2.499992549e-01f, -2.777458727e-02f,
                             1.729921903e-03f, -6.387370377e-05f};
@@ -549,17 +561,70 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f64(EvalPlan P, TablesDev t, do
 // Partials per direction: LAPLACE / BESSEL: n sums  sum Delta kappa(s) x_k;
 // FOURIER: 2n sums  (sum Delta cos(s) x_k, sum Delta sin(s) x_k)  [d Re = +cos, d Im = -sin].
 
+// Packed adjoint over staged points [ws, we) for one direction pair per lane:
+//   g_k += v kappa(z) x_k  (Fourier: g_k += v cos z x_k and g_{n+k} += v sin z x_k)
+// with x_k rebuilt from the staged integer p_k as x_k = p_k * xa_k + xb_k.  Blocks of
+// four points are summed by FMA, then added with compensation (as the forward).
+template <int NDIM, int KERNEL, int PATH>
+__device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int we, const float2 (&w)[3],
+                                                    const float2 (&xa)[3], const float2 (&xb)[3],
+                                                    float2 (&s2)[(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM],
+                                                    float2 (&n2)[(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM]) {
+    constexpr int NC = (KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM;
+    constexpr int BLK = 4;
+    for (int e = ws; e < we; e += BLK) {
+        float2 blk[NC];
+#pragma unroll
+        for (int u = 0; u < BLK; ++u) {
+            const float4 qa = A[2 * (e + u)];
+            const float4 qb = A[2 * (e + u) + 1];
+            const float2 pc[3] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y)};
+            const float2 v2 = make_float2(qb.z, qb.w);
+            float2 z = mul2(pc[0], w[0]);
+            z = fma2(pc[1], w[1], z);
+            if (NDIM == 3) z = fma2(pc[2], w[2], z);
+            float2 x[3];
+#pragma unroll
+            for (int k = 0; k < NDIM; ++k) x[k] = fma2(pc[k], xa[k], xb[k]);
+            float2 t[2];
+            if (KERNEL == TOPOT_LAPLACE) {
+                t[0] = mul2(v2, make_float2(ex2_approx(z.x), ex2_approx(z.y)));
+            } else if (KERNEL == TOPOT_FOURIER) {
+                const float2 ww = mul2(z, z);
+                const float2 sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
+                const float2 cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
+                t[0] = mul2(v2, cs);
+                t[1] = mul2(v2, sn);
+            } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
+                const float2 y = mul2(z, z);
+                const float2 j1 = mul2(z, PATH == 2 ? j1q_short2(y) : j1q_long2(y));
+                t[0] = mul2(make_float2(-v2.x, -v2.y), j1);
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float2 tc = t[c / NDIM];
+                const float2 xc = x[c % NDIM];
+                blk[c] = u == 0 ? mul2(tc, xc) : fma2(tc, xc, blk[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) kahan2_add(s2[c], n2[c], blk[c]);
+    }
+}
+
 template <int NDIM, int KERNEL, int DL, typename Tval>
 __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t, double* part) {
     constexpr int NK = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr int NC = NK * NDIM;
     constexpr int TDH = 32 * DL;
     constexpr int NO = 1 << NDIM;
-    __shared__ float4 A[kHtSub / 2];
-    __shared__ float4 X[kHtSub / 2];
+    constexpr int SUB = kHtSub / 2;
+    // scalar path: A[0, SUB) = (p0, p1, p2, v), X = A + SUB = (x0, x1, x2); packed path:
+    // (p0, p0, p1, p1), (p2, p2, v, v) per point over the whole buffer
+    __shared__ __align__(16) float4 A[2 * SUB];
+    float4* X = A + SUB;
     __shared__ double red[kHtWarps][TDH * NC];
     __shared__ long long sh_item;
-    constexpr int SUB = kHtSub / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long nitems = P.ctl[2];
 
@@ -580,7 +645,60 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
 
-        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+        float mloc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+            if (hd[j].valid)
+                mloc = fmaxf(mloc, (float)(0.5 * (fabs(hd[j].xi[0]) + fabs(hd[j].xi[1]) + fabs(hd[j].xi[2]))));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+        int path = 0;   // packed paths: as the forward, one direction pair per lane
+        if (DL == 2) {
+            if (KERNEL == TOPOT_LAPLACE) path = 1;
+            else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
+            else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
+        }
+        if constexpr (DL == 2) {
+            if (path != 0) {
+                const float wsc = KERNEL == TOPOT_BESSEL ? 0.5f : 1.0f;
+                float2 w[3], xa[3], xb[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    w[k] = make_float2(wsc * hd[0].w[k], wsc * hd[1].w[k]);
+                    const float mk1 = (float)(it.I->m[k] - 1);
+                    if (KERNEL == TOPOT_LAPLACE) {   // x = sigma (q / (m - 1) + 1/2), sigma = eps_k
+                        const float sg = ((it.o >> k) & 1) ? -1.0f : 1.0f;
+                        xa[k] = make_float2(sg / mk1, sg / mk1);
+                        xb[k] = make_float2(0.5f * sg, 0.5f * sg);
+                    } else {                          // x = c / (2 (m - 1))
+                        xa[k] = make_float2(0.5f / mk1, 0.5f / mk1);
+                        xb[k] = make_float2(0.0f, 0.0f);
+                    }
+                }
+                float2 s2[NC], n2[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) s2[c] = n2[c] = make_float2(0.0f, 0.0f);
+                for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+                    const int cnt = (int)min((long long)SUB, it.e_end - e0);
+                    __syncthreads();
+                    const int cnt_pad = (cnt + kHtWarps * 8 - 1) / (kHtWarps * 8) * (kHtWarps * 8);
+                    ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr, cnt_pad);
+                    __syncthreads();
+                    const int per = cnt_pad / kHtWarps;
+                    const int ws = warp * per, we = ws + per;
+                    if (path == 2) ht_adj_packed_range<NDIM, KERNEL, 2>(A, ws, we, w, xa, xb, s2, n2);
+                    else ht_adj_packed_range<NDIM, KERNEL, 1>(A, ws, we, w, xa, xb, s2, n2);
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    acc[0][c] = s2[c].x;
+                    cmp[0][c] = -n2[c].x;
+                    acc[1][c] = s2[c].y;
+                    cmp[1][c] = -n2[c].y;
+                }
+            }
+        }
+        for (long long e0 = it.e_begin; path == 0 && e0 < it.e_end; e0 += SUB) {
             const int cnt = (int)min((long long)SUB, it.e_end - e0);
             __syncthreads();
             ht_stage<NDIM, KERNEL, true, Tval>(t, it, e0, cnt, A, X);
