@@ -79,7 +79,7 @@ typedef struct topot_tables topot_tables;   /* opaque; owns the device tables */
 /* Tile shapes of the evaluation kernels, per operation; 0 = library default.  Set by
  * the autotuner of the Python binding, or by hand. */
 typedef struct {
-    int ect_dirs_per_warp;    /* ECT / Radon: 8, 16 or 32 directions share one warp       */
+    int ect_dirs_per_warp;    /* ECT / Radon: 8, 16, 32 per warp, or 64 (two per lane)    */
     int ect_chunk;            /* ECT / Radon: critical points per work item (x256)        */
     int ect_ctas_per_sm;      /* ECT / Radon: resident blocks per SM of the persistent grid */
     int ht_dirs_per_lane;     /* hybrid FP32C: 1, 2, 4 (8: Laplace) directions per lane    */

@@ -21,7 +21,7 @@ CACHE = os.environ.get("TOPOT_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json"))
 
 ECT_SPACE = [dict(ect_dirs_per_warp=td, ect_chunk=ch, ect_ctas_per_sm=c)
-             for td in (8, 16, 32) for ch in (0, 16384, 131072) for c in (0, 1)]
+             for td in (8, 16, 32, 64) for ch in (0, 16384, 131072) for c in (0, 1)]
 HT_SPACE = [dict(ht_dirs_per_lane=dl, ht_chunk=ch, ht_ctas_per_sm=c)
             for dl in (1, 2, 4, 8) for ch in (0, 16384, 131072) for c in (0, 3)]
 

@@ -129,13 +129,13 @@ bool valid_dirs_args(const topot_tables* t, const void* d_dirs, int D, int per_i
     return t && d_dirs && D >= 1 && (per_image_dirs == 0 || per_image_dirs == 1);
 }
 
+// Directions per ECT work item: 8, 16 or 32 per warp, or 64 (two per lane).
 int hist_tile(const topot_tables* t, int D, int nsets_dirs_per_orthant, int T) {
     int td = t->tuning.ect_dirs_per_warp;
-    if (td != 8 && td != 16 && td != 32) {
-        td = 32;
+    if (td != 8 && td != 16 && td != 32 && td != 64) {
         const int per_orthant = nsets_dirs_per_orthant;
-        if (per_orthant < 24) td = 16;
-        if (per_orthant < 12) td = 8;
+        // 64 (two per lane) halves the blocks per SM; measured slower, left to the autotuner
+        td = per_orthant >= 24 ? 32 : (per_orthant >= 12 ? 16 : 8);
     }
     (void)D;
     while (td > 8 && hist_smem_bytes(td, T) > 200 * 1024) td >>= 1;
@@ -378,7 +378,8 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
         return TOPOT_OK;
     }
     const topot_tuning& u = *tuning;
-    if ((u.ect_dirs_per_warp && u.ect_dirs_per_warp != 8 && u.ect_dirs_per_warp != 16 && u.ect_dirs_per_warp != 32) ||
+    if ((u.ect_dirs_per_warp && u.ect_dirs_per_warp != 8 && u.ect_dirs_per_warp != 16 &&
+         u.ect_dirs_per_warp != 32 && u.ect_dirs_per_warp != 64) ||
         (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4 &&
          u.ht_dirs_per_lane != 8) ||
         u.ect_chunk < 0 || (u.ect_chunk % 256) != 0 || u.ht_chunk < 0 || (u.ht_chunk % 256) != 0 ||

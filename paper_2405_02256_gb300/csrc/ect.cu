@@ -85,16 +85,21 @@ __device__ __noinline__ int exact_bin(float c0, float c1, float c2, const double
     }
 }
 
-template <int NDIM, int TD, typename Tval>
-__global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t, int32_t* out_lo,
-                                                     int32_t* out_hi) {
+template <int NDIM, int TD, int DPL, typename Tval>
+__global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan P, TablesDev t, int32_t* out_lo,
+                                                                     int32_t* out_hi) {
+    // TD directions share a warp (lane = direction for TD = 32; 32/TD point groups
+    // otherwise); with DPL = 2 every lane bins two directions (64 per warp), which halves
+    // the per-update instruction overhead at the cost of a twice larger histogram.
     constexpr int NW = kHistBlock / 32;
     constexpr int G = 32 / TD;
     constexpr int NO = 1 << NDIM;
+    constexpr int TDT = TD * DPL;                           // directions per work item
+    static_assert(DPL == 1 || TD == 32, "two directions per lane only with 32 per warp");
     extern __shared__ float4 stage[];                       // [kHistSub]
-    int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [TD][T + 1]
+    int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [TDT][T + 1]
     __shared__ long long sh_item;
-    __shared__ int sh_dir[TD];
+    __shared__ int sh_dir[TDT];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = P.T;
@@ -120,23 +125,28 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
         const int set = P.nsets == 1 ? 0 : b;
         const int* bo = P.boff + (long long)set * (NO + 1);
         const int nd = bo[o + 1] - bo[o];
-        const int r = tile * TD + dl;
-        const bool dvalid = r < nd;
-        const int d = dvalid ? P.perm[(long long)set * P.D + bo[o] + r] : 0;
-        if (tid < TD) sh_dir[tid] = dvalid ? d : -1;
-        double xi[3] = {0.0, 0.0, 0.0};
-        const double* xp = P.dirs + ((long long)set * P.D + d) * NDIM;
+        double xi[DPL][3];
+        DirCoef cf[DPL];
+        int* row[DPL];
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) xi[k] = xp[k];
-        const DirCoef cf = make_coef(xi, NDIM, I.m, P.t_min, P.t_max, T);
+        for (int j = 0; j < DPL; ++j) {
+            const int r = tile * TDT + j * TD + dl;
+            const bool dvalid = r < nd;
+            const int d = dvalid ? P.perm[(long long)set * P.D + bo[o] + r] : 0;
+            if (g == 0 && warp == 0) sh_dir[j * TD + dl] = dvalid ? d : -1;
+            const double* xp = P.dirs + ((long long)set * P.D + d) * NDIM;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xi[j][k] = k < NDIM ? xp[k] : 0.0;
+            cf[j] = make_coef(xi[j], NDIM, I.m, P.t_min, P.t_max, T);
+            row[j] = hist + (j * TD + dl) * HS;   // lanes of directions past the tile end
+        }                                          // bin into rows nobody reads
 
-        for (int i = tid; i < TD * HS; i += kHistBlock) hist[i] = 0;
+        for (int i = tid; i < TDT * HS; i += kHistBlock) hist[i] = 0;
 
         const long long N = t.seg_count[(long long)b * t.S + seg];
         const long long base = I.seg_base + (long long)seg * I.N;
         const long long e_begin = (long long)ch * chunk;
         const long long e_end = min(N, e_begin + chunk);
-        const int* hrow = hist + dl * HS;
 
         // Staging is software-pipelined: the raw entries of the next round are loaded
         // into registers while the current round is binned.
@@ -183,46 +193,55 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
                 const int gl = (((len + G - 1) / G) + 3) & ~3;
                 const int gs = ws + g * gl;
                 const int ge = min(we, gs + gl);
-                int* row = const_cast<int*>(hrow);
                 const float umax = (float)T - 0.5f;
                 // Bin from u without float->int conversions: adding 1.5 * 2^23 rounds u to
                 // an integer r (ties to even) held in the low mantissa bits.  u is clamped to
                 // [-0.5, T - 0.5] first, so the sublevel bin ceil(u) and the superlevel index
                 // floor(u) + 1 both land in [0, T].  Points within delta of a bin edge are
                 // binned exactly on a slow path, checked once per 4 points.
-                // Lanes of directions past the tile end bin into rows nobody reads.
                 for (int e = gs; e < ge; e += 4) {
-                    bool amb[4];
+                    bool amb[4][DPL];
                     bool any = false;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float4 q = stage[e + k];
-                        float u;
-                        if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
-                        else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
-                        const float uc = fminf(fmaxf(u, -0.5f), umax);
-                        const float f = uc + 12582912.0f;
-                        const float rf = f - 12582912.0f;
-                        const int r = __float_as_int(f) - 0x4B400000;
-                        const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
-                        amb[k] = !(fabsf(u - rf) >= cf.delta);
-                        any |= amb[k];
-                        if (!amb[k]) atomicAdd(&row[bin], __float_as_int(q.w));
+#pragma unroll
+                        for (int j = 0; j < DPL; ++j) {
+                            float u;
+                            if (NDIM == 3)
+                                u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
+                            else
+                                u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
+                            const float uc = fminf(fmaxf(u, -0.5f), umax);
+                            const float f = uc + 12582912.0f;
+                            const float rf = f - 12582912.0f;
+                            const int r = __float_as_int(f) - 0x4B400000;
+                            const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
+                            amb[k][j] = !(fabsf(u - rf) >= cf[j].delta);
+                            any |= amb[k][j];
+                            if (!amb[k][j]) atomicAdd(&row[j][bin], __float_as_int(q.w));
+                        }
                     }
                     // rare: exact FP64 binning.  A per-lane branch: lane groups of one warp
                     // may run different trip counts, so no warp-wide vote may be used here.
                     if (any) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            if (amb[k]) {
-                                const float4 q = stage[e + k];
-                                float u;
-                                if (NDIM == 3) u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, fmaf(q.z, cf.a2, cf.beta)));
-                                else u = fmaf(q.x, cf.a0, fmaf(q.y, cf.a1, cf.beta));
-                                const int bin = maxbin
-                                                    ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi, I.m, P.thr, T, u)
-                                                    : exact_bin<NDIM, false>(q.x, q.y, q.z, xi, I.m, P.thr, T, u);
-                                atomicAdd(&row[bin], __float_as_int(q.w));
+#pragma unroll
+                            for (int j = 0; j < DPL; ++j) {
+                                if (amb[k][j]) {
+                                    const float4 q = stage[e + k];
+                                    float u;
+                                    if (NDIM == 3)
+                                        u = fmaf(q.x, cf[j].a0,
+                                                 fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
+                                    else
+                                        u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
+                                    const int bin =
+                                        maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u)
+                                               : exact_bin<NDIM, false>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u);
+                                    atomicAdd(&row[j][bin], __float_as_int(q.w));
+                                }
                             }
                         }
                     }
@@ -232,7 +251,7 @@ __global__ void __launch_bounds__(kHistBlock, 2) k_hist(EvalPlan P, TablesDev t,
         __syncthreads();
         int32_t* out = maxbin ? out_hi : out_lo;
         const int off = maxbin ? 1 : 0;
-        for (int i = tid; i < TD * T; i += kHistBlock) {
+        for (int i = tid; i < TDT * T; i += kHistBlock) {
             const int q = i / T;
             const int j = i - q * T;
             const int v = hist[q * HS + j + off];
@@ -296,7 +315,7 @@ static cudaError_t launch_hist_n(const EvalPlan& P, const TablesDev& t, int td, 
     const size_t smem = sizeof(float4) * kHistSub + sizeof(int) * (size_t)td * (P.T + 1);
 #define TOPOT_HIST_CASE(TDV)                                                                   \
     case TDV: {                                                                                \
-        auto k = k_hist<NDIM, TDV, Tval>;                                                      \
+        auto k = k_hist<NDIM, (TDV > 32 ? 32 : TDV), (TDV > 32 ? 2 : 1), Tval>;                \
         static cudaError_t attr = set_smem_attrs(reinterpret_cast<const void*>(k));            \
         if (attr != cudaSuccess) return attr;                                                  \
         k<<<grid, kHistBlock, smem, st>>>(P, t, lo, hi);                                       \
@@ -306,6 +325,7 @@ static cudaError_t launch_hist_n(const EvalPlan& P, const TablesDev& t, int td, 
         TOPOT_HIST_CASE(8)
         TOPOT_HIST_CASE(16)
         TOPOT_HIST_CASE(32)
+        TOPOT_HIST_CASE(64)
         default: return cudaErrorInvalidValue;
     }
 #undef TOPOT_HIST_CASE

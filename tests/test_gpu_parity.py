@@ -135,7 +135,7 @@ def test_ect_per_image_directions(tb):
         np.testing.assert_array_equal(got_r[b], O.radon_grid(ref, dirs[b], -0.8, 0.8, 33))
 
 
-@pytest.mark.parametrize("td", [8, 16, 32])
+@pytest.mark.parametrize("td", [8, 16, 32, 64])
 def test_ect_tile_shapes(tb, td):
     img = synth.grf((120, 130), 5.0, seed=40)
     ref = O.critical_tables(img)
