@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     int* sh_int = reinterpret_cast<int*>(smem_raw + 16);               // [8]
     long long* sh_pref = reinterpret_cast<long long*>(smem_raw + 48);  // [S]
     long long* sh_acc = sh_pref + S;                                   // [1 + NO]
-    int* sh_cnt = reinterpret_cast<int*>(sh_acc + 1 + NO);             // [S][K][NW]
-    size_t stage_off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * K * NW;
+    int* sh_cnt = reinterpret_cast<int*>(sh_acc + 1 + NO);             // [S][NW]
+    size_t stage_off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * NW;
     stage_off = (stage_off + 15) & ~size_t(15);
     Tin* stage = reinterpret_cast<Tin*>(smem_raw + stage_off);
 
@@ -188,9 +188,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     __syncthreads();
 
     // ---- 2. lower-star values, kept in registers --------------------------------------
-    // Vertex j of the tile (j = k * BLOCK + tid) has linear index L0 + j: the tile is a run
-    // of full rows (cols == m0) or part of one row.  Its staged position is tracked as
-    // (r, c) incrementally instead of dividing by the row length.
+    // Blocked layout: thread tid owns the K consecutive vertices j = tid * K + k of the
+    // tile, whose linear indices are L0 + j (the tile is a run of full rows, cols == m0, or
+    // part of one row).  Their staged positions (r, c) are tracked incrementally.
     int vals[K][NO];
     int chi_acc = 0;          // |Delta^-| <= 2^(n-1) * 255 per vertex for u8, and int32 input
     int abs_acc[NO];          // is limited to |phi| < 2^26 (checked below): K vertices fit int32
@@ -198,16 +198,17 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     for (int o = 0; o < NO; ++o) abs_acc[o] = 0;
     bool bad_pixel = false;
     const Tin* center0 = stage + (NP == 3 ? PS : 0) + RS + PAD;
+    const int j0 = tid * K;
     {
         const int W = cols;
-        int r = 0, c = tid;
-        if (rows > 1) { r = (int)fastdiv((uint32_t)tid, I.div0); c = tid - r * W; }
-        const int dq = rows > 1 ? BLOCK / W : 0;
-        const int dr = BLOCK - dq * W;
+        int r = 0, c = j0;
+        if (rows > 1 && j0 < nverts) {
+            r = (int)fastdiv((uint32_t)j0, I.div0);
+            c = j0 - r * W;
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int j = k * BLOCK + tid;
-            if (j < nverts) {
+            if (j0 + k < nverts) {
                 const Tin* cp = center0 + r * RS + c;
                 lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
                 if constexpr (PT::kSigned) {
@@ -221,9 +222,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
 #pragma unroll
                 for (int o = 0; o < NO; ++o) vals[k][o] = 0;
             }
-            c += dr;
-            r += dq;
-            if (c >= W) { c -= W; ++r; }
+            if (++c == W) {
+                c = 0;
+                ++r;
+            }
         }
     }
     if (bad_pixel) dev_set_error(T.err, kDevErrOverflow);
@@ -232,14 +234,23 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
         return s < NO ? vals[k][s] : vals[k][s - NO] - vals[k][(s - NO) ^ (NO - 1)];
     };
 
-    // ---- 3a. per-warp counts ------------------------------------------------------------
+    // ---- 3a. per-thread counts, warp-inclusive scans --------------------------------------
+    int incl[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) c += seg_value(k, s) != 0;
+        incl[s] = c;
+    }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const unsigned bal = __ballot_sync(0xffffffffu, seg_value(k, s) != 0);
-            if (lane == 0) sh_cnt[(s * K + k) * NW + warp] = __popc(bal);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl[s], d);
+            if (lane >= d) incl[s] += y;
         }
+        if (lane == 31) sh_cnt[s * NW + warp] = incl[s];
     }
     // chi and sum |Delta^-| of the tile (64-bit from the warp level up)
     const long long chi_w = warp_sum((long long)chi_acc);
@@ -254,12 +265,12 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     }
     __syncthreads();
 
-    // ---- 3b. block scan per segment + decoupled look-back --------------------------------
+    // ---- 3b. scan of the warp totals per segment + decoupled look-back ---------------------
     if (tid < S) {
         const int s = tid;
         int run = 0;
-        int* cs = sh_cnt + s * K * NW;
-        for (int q = 0; q < K * NW; ++q) {
+        int* cs = sh_cnt + s * NW;
+        for (int q = 0; q < NW; ++q) {
             const int c = cs[q];
             cs[q] = run;
             run += c;
@@ -303,22 +314,24 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     }
     __syncthreads();
 
-    // ---- 3c. scatter the compacted entries, one segment at a time -----------------------
-    const unsigned lt_mask = lanemask_lt();
-    const int vbase = (int)L0 + tid;          // linear index of vertex k = 0 (N < 2^31)
+    // ---- 3c. every thread writes its own run of entries, segment by segment ---------------
+    const int vbase = (int)L0 + j0;           // linear index of this thread's first vertex
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        int* __restrict__ didx = T.arena_idx + sh_pref[s];
-        Tval* __restrict__ dval = reinterpret_cast<Tval*>(T.arena_val) + sh_pref[s];
-        const int* cnt_s = sh_cnt + s * K * NW + warp;
+        int c = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) c += seg_value(k, s) != 0;
+        const long long pos0 = sh_pref[s] + sh_cnt[s * NW + warp] + incl[s] - c;
+        int* __restrict__ didx = T.arena_idx + pos0;
+        Tval* __restrict__ dval = reinterpret_cast<Tval*>(T.arena_val) + pos0;
+        int q = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int v = seg_value(k, s);
-            const unsigned bal = __ballot_sync(0xffffffffu, v != 0);
             if (v != 0) {
-                const int pos = cnt_s[k * NW] + __popc(bal & lt_mask);
-                didx[pos] = vbase + k * BLOCK;
-                dval[pos] = (Tval)v;
+                didx[q] = vbase + k;
+                dval[q] = (Tval)v;
+                ++q;
             }
         }
     }
@@ -349,7 +362,7 @@ int extract_k(int n) { return n == 2 ? 8 : 4; }
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows) {
     const int NO = 1 << n, S = NO + NO / 2;
     const int NW = extract_block(n) / 32;
-    size_t off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * extract_k(n) * NW;
+    size_t off = 48 + sizeof(long long) * (S + 1 + NO) + sizeof(int) * S * NW;
     off = (off + 15) & ~size_t(15);
     const int NP = n == 3 ? 3 : 1;
     return off + (size_t)NP * stage_rows * row_stride * elem_bytes;
