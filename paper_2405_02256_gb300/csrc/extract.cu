@@ -20,10 +20,6 @@
 
 namespace topot {
 
-constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate available
-constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix available
-constexpr unsigned long long kCountMask = (1ull << 62) - 1;
-
 template <typename Tin> struct PixTraits;
 template <> struct PixTraits<uint8_t> {
     // u8 values are >= 0: a zero sentinel makes the minimum over any box that leaves

@@ -62,6 +62,11 @@ struct ImgDesc {
     int tiles_per_plane;    // ceil(m_1 / R) * segs_per_row
     FastDiv div0;           // division by m_0
     FastDiv div1;           // division by m_1
+    // 2-D 8-bit fast path only: strips of 8 vertices per tile row, staged row stride
+    int spr;                // ceil(W / 8)
+    int rs;                 // staged row stride (bytes, multiple of 16)
+    FastDiv div_spr;        // division by spr
+    FastDiv div_segs;       // division by segs_per_row
 };
 
 // Device view of a tables handle.
@@ -88,7 +93,13 @@ struct ExtractArgs {
     unsigned long long* status;       // [num_tiles * S] look-back words, zeroed before launch
     int row_stride;                   // staged row stride (elements, 16-byte multiple)
     int stage_rows;                   // staged rows per plane (max R + 2)
+    int stage_bytes;                  // 2-D 8-bit fast path: max over images of (R + 2) * rs
 };
+
+// Look-back status words of the extraction kernels: 2-bit flag + 62-bit count.
+constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate available
+constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix available
+constexpr unsigned long long kCountMask = (1ull << 62) - 1;
 
 __device__ __forceinline__ void dev_set_error(unsigned* err, unsigned bit) {
     atomicOr(err, bit);

@@ -37,6 +37,10 @@ def _images():
         "tiny2x2": np.array([[3, 1], [2, 5]], dtype=np.uint8),
         "tall700x5": synth.uniform_u8((700, 5), seed=4),
         "const": np.full((33, 17), 7, dtype=np.uint8),
+        "narrow1500x8": synth.uniform_u8((1500, 8), seed=13),
+        "narrow1030x9": synth.grf((1030, 9), 3.0, seed=14),
+        "grf20x4096": synth.grf((20, 4096), 6.0, seed=15),
+        "wide2x4097": synth.uniform_u8((2, 4097), seed=16),
         "bern9x10x11": synth.bernoulli((9, 10, 11), 0.5, seed=6),
         "grf20x33x64": synth.grf((20, 33, 64), 4.0, seed=7),
         "cube2": np.full((2, 2, 2), 1, dtype=np.uint8),
