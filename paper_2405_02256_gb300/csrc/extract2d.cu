@@ -417,24 +417,57 @@ __global__ void __launch_bounds__(kB, 2) k_extract2d_u8(ExtractArgs p) {
     __syncthreads();
 
     // ---- 6. write the tile's runs; chi and sum |Delta^-_o| from the lower tables -------------
+    // Each segment's run starts at an arbitrary arena position g0.  It is written in groups
+    // of four arena slots aligned to four (one 16-byte index store, one 8-byte value store);
+    // the partial groups at the two ends store entry by entry.  Group numbers continue
+    // across segments modulo the block size, so that every thread gets about the same
+    // number of groups.
     int chi = 0, ab[4] = {0, 0, 0, 0};
     {
-        int16_t* __restrict__ aval = reinterpret_cast<int16_t*>(T.arena_val);
-        int* __restrict__ aidx = T.arena_idx;
-        uint32_t base = 0;
+        uint32_t base = 0, cum = 0;
 #pragma unroll
         for (int s = 0; s < kSeg; ++s) {
             const int n = (int)field16(tot, s);
             const long long g0 = sh_pref[s];
-            for (int e = tid; e < n; e += kB) {
-                const uint32_t w = out[base + e];
-                const int v = (int)__half2short_rn(__ushort_as_half((unsigned short)(w & 0xffffu)));
-                aidx[g0 + e] = L0 + (int)(w >> 16);
-                aval[g0 + e] = (int16_t)v;
-                if (s < 4) ab[s & 3] += abs(v);
-                if (s == 0) chi += v;
+            const int ph = (int)(g0 & 3);
+            const int ngroups = (ph + n + 3) >> 2;
+            int* __restrict__ pi = T.arena_idx + (g0 - ph);
+            int16_t* __restrict__ pv = reinterpret_cast<int16_t*>(T.arena_val) + (g0 - ph);
+            const uint32_t* o = out + base;
+            for (int q = (int)(((uint32_t)tid - cum) & (kB - 1)); q < ngroups; q += kB) {
+                const int e0 = 4 * q - ph;                  // entry of the group's first slot
+                int id[4], v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = e0 + k;
+                    id[k] = 0;
+                    v[k] = 0;
+                    if (e >= 0 && e < n) {
+                        const uint32_t w = o[e];
+                        v[k] = (int)__half2short_rn(__ushort_as_half((unsigned short)(w & 0xffffu)));
+                        id[k] = L0 + (int)(w >> 16);
+                    }
+                    if (s < 4) ab[s & 3] += abs(v[k]);
+                    if (s == 0) chi += v[k];
+                }
+                if (e0 >= 0 && e0 + 4 <= n) {
+                    *reinterpret_cast<int4*>(pi + 4 * q) = make_int4(id[0], id[1], id[2], id[3]);
+                    *reinterpret_cast<uint2*>(pv + 4 * q) =
+                        make_uint2(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x5410),
+                                   __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x5410));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = e0 + k;
+                        if (e >= 0 && e < n) {
+                            pi[4 * q + k] = id[k];
+                            pv[4 * q + k] = (int16_t)v[k];
+                        }
+                    }
+                }
             }
             base += (uint32_t)n;
+            cum += (uint32_t)ngroups;
         }
     }
     const int red[5] = {chi, ab[0], ab[1], ab[2], ab[3]};
