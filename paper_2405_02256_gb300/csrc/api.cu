@@ -15,10 +15,10 @@ cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaS
 int extract_block(int n);
 int extract_k(int n);
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
-cudaError_t launch_extract2d_u8(const ExtractArgs& a, cudaStream_t st);
-int extract2d_tile_vertices();
-int extract2d_threads();
-size_t extract2d_smem_bytes(int stage_bytes);
+cudaError_t launch_extract_u8(int n, const ExtractArgs& a, cudaStream_t st);
+int extract_u8_threads(int n);
+int extract_u8_strip(int n);
+size_t extract_u8_smem_bytes(int n, int stage_bytes);
 size_t hist_smem_bytes(int td, int T);
 cudaError_t launch_hist(const EvalPlan& P, const TablesDev& t, int td, int32_t* lo, int32_t* hi, int grid,
                         cudaStream_t st);
@@ -42,7 +42,7 @@ struct topot_tables {
     long long total_entries = 0;
     long long num_tiles = 0;
     int row_stride = 0, stage_rows = 0;
-    bool fast2d = false;      // 2-D 8-bit batch: extraction by k_extract2d_u8
+    bool u8 = false;          // 8-bit batch: extraction by k_extract_u8
     int stage_bytes = 0;      // its staged bytes per tile (max over images)
     // device memory
     void* meta = nullptr;             // one block: img, seg_count, chi, absum, err, ticket, status
@@ -183,7 +183,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
     const int tile_v = extract_block(n) * extract_k(n);
     const int NP = n == 3 ? 3 : 1;
     const size_t smem_budget = 96 * 1024;
-    t->fast2d = n == 2 && dtype == TOPOT_U8;
+    t->u8 = dtype == TOPOT_U8;
     long long tiles = 0, entries = 0;
     int max_w = 1, max_r = 1;
     t->h_img.resize(B);
@@ -210,13 +210,16 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         entries += N * t->S;
         I.tile_begin = tiles;
         const int m0 = I.m[0], m1 = I.m[1];
-        if (t->fast2d) {
-            // strips of 8 vertices, one per thread; R full rows or one piece of a row
-            I.W = std::min(m0, extract2d_tile_vertices());
-            I.spr = (I.W + 7) / 8;
-            I.R = I.W == m0 ? std::max(1, std::min(extract2d_threads() / I.spr, m1)) : 1;
-            I.rs = (int)align_up((size_t)(16 + 8 * I.spr + 1), 16);
-            t->stage_bytes = std::max(t->stage_bytes, (I.R + 2) * I.rs);
+        if (t->u8) {
+            // strips of `strip` vertices, one per thread; R full rows or one piece of a row
+            const int strip = extract_u8_strip(n), threads = extract_u8_threads(n);
+            I.W = std::min(m0, threads * strip);
+            I.spr = (I.W + strip - 1) / strip;
+            I.R = I.W == m0 ? std::max(1, std::min(threads / I.spr, m1)) : 1;
+            // rows contiguous in the stage when whole rows are 16-byte aligned in the image
+            I.packed = I.W == m0 && m0 % 16 == 0 && h_offsets[b] % 16 == 0;
+            I.rs = I.packed ? m0 : (int)align_up((size_t)(16 + strip * I.spr + 1), 16);
+            t->stage_bytes = std::max(t->stage_bytes, NP * (I.R + 2) * I.rs + 32);
         } else if (m0 <= tile_v) {
             I.W = m0;
             I.R = std::max(1, std::min(tile_v / m0, m1));
@@ -234,6 +237,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         I.div1 = make_fastdiv((uint32_t)m1);
         I.div_spr = make_fastdiv((uint32_t)std::max(1, I.spr));
         I.div_segs = make_fastdiv((uint32_t)I.segs_per_row);
+        I.div_tpp = make_fastdiv((uint32_t)I.tiles_per_plane);
         max_w = std::max(max_w, I.W);
         max_r = std::max(max_r, I.R);
     }
@@ -280,7 +284,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         free_tables(t);
         return cuda_fail(e, "tables_create: initialise metadata");
     }
-    const size_t smem = t->fast2d ? extract2d_smem_bytes(t->stage_bytes)
+    const size_t smem = t->u8 ? extract_u8_smem_bytes(n, t->stage_bytes)
                                   : extract_smem_bytes(n, elem, t->row_stride, t->stage_rows);
     if (smem > 200 * 1024) {
         free_tables(t);
@@ -304,8 +308,8 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     a.row_stride = t->row_stride;
     a.stage_rows = t->stage_rows;
     a.stage_bytes = t->stage_bytes;
-    if (t->fast2d)
-        TOPOT_CUDA(launch_extract2d_u8(a, st));
+    if (t->u8)
+        TOPOT_CUDA(launch_extract_u8(t->n, a, st));
     else
         TOPOT_CUDA(launch_extract(t->n, t->dtype, a, st));
     return TOPOT_OK;

@@ -1,4 +1,5 @@
-// K1: critical-table extraction (Section 3, Delta^-; Section 4.2, preprocessing).
+// K1: critical-table extraction for int32 pixels (Section 3, Delta^-; Section 4.2,
+// preprocessing).  8-bit images and volumes use k_extract_u8 (extract_u8.cu).
 //
 // One block per tile.  A tile is a run of vertices that is contiguous in linear
 // vertex order: R full rows of one plane (m_0 <= W) or one W-wide piece of a row.
@@ -365,12 +366,10 @@ size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows)
 }
 
 cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st) {
-    const size_t smem = extract_smem_bytes(n, dtype == TOPOT_U8 ? 1 : 4, a.row_stride, a.stage_rows);
-    if (n == 2) {
-        if (dtype == TOPOT_U8) return launch_extract_t<2, uint8_t, int16_t, 256, 8>(a, smem, st);
-        return launch_extract_t<2, int32_t, int32_t, 256, 8>(a, smem, st);
-    }
-    if (dtype == TOPOT_U8) return launch_extract_t<3, uint8_t, int16_t, 256, 4>(a, smem, st);
+    // 8-bit batches go to k_extract_u8 (extract_u8.cu)
+    if (dtype != TOPOT_I32) return cudaErrorInvalidValue;
+    const size_t smem = extract_smem_bytes(n, 4, a.row_stride, a.stage_rows);
+    if (n == 2) return launch_extract_t<2, int32_t, int32_t, 256, 8>(a, smem, st);
     return launch_extract_t<3, int32_t, int32_t, 256, 4>(a, smem, st);
 }
 

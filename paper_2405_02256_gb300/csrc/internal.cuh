@@ -62,11 +62,13 @@ struct ImgDesc {
     int tiles_per_plane;    // ceil(m_1 / R) * segs_per_row
     FastDiv div0;           // division by m_0
     FastDiv div1;           // division by m_1
-    // 2-D 8-bit fast path only: strips of 8 vertices per tile row, staged row stride
-    int spr;                // ceil(W / 8)
+    // 8-bit extraction kernel only: strips of vertices per tile row, staged row stride
+    int spr;                // ceil(W / strip)
     int rs;                 // staged row stride (bytes, multiple of 16)
+    int packed;             // 1: full-row tiles, m_0 and offset multiples of 16 (rs = m_0)
     FastDiv div_spr;        // division by spr
     FastDiv div_segs;       // division by segs_per_row
+    FastDiv div_tpp;        // division by tiles_per_plane
 };
 
 // Device view of a tables handle.
@@ -93,7 +95,7 @@ struct ExtractArgs {
     unsigned long long* status;       // [num_tiles * S] look-back words, zeroed before launch
     int row_stride;                   // staged row stride (elements, 16-byte multiple)
     int stage_rows;                   // staged rows per plane (max R + 2)
-    int stage_bytes;                  // 2-D 8-bit fast path: max over images of (R + 2) * rs
+    int stage_bytes;                  // 8-bit kernel: staged bytes per tile (max over images)
 };
 
 // Look-back status words of the extraction kernels: 2-bit flag + 62-bit count.

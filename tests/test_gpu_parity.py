@@ -85,6 +85,20 @@ def test_tables_ragged_batch(tb):
         _check_tables(tabs, b, img)
 
 
+def test_tables_unaligned_pixel_buffer(tb):
+    # whole rows 16-byte aligned relative to the buffer, but the buffer itself starts one
+    # byte past a 16-byte boundary: the staging falls back from bulk copies to plain loads
+    imgs = [synth.grf((40, 64), 4.0, seed=90), synth.grf((6, 10, 32), 3.0, seed=91)]
+    for img in imgs:
+        b = tb.pack_images([img])
+        px = torch.zeros(b.pixels.numel() + 1, dtype=torch.uint8, device="cuda")
+        px[1:] = b.pixels
+        tabs = tb.tables_create(b.shapes, b.offsets)
+        tabs.build(px[1:])
+        tabs.sync()
+        _check_tables(tabs, 0, img)
+
+
 def _dirs_2d():
     d = [synth.circle_dirs(32), synth.random_2d_dirs(40, 3, 0.01, 1.0),
          np.array([[0.0, 1.0], [1.0, 0.0], [-0.0, -1.0], [-1.0, -0.0], [0.0, 0.0], [1.0, 1.0], [1.0, -1.0]])]
