@@ -36,6 +36,11 @@ B_IMAGES, SIDE, ELL = 64, 2048, 16.0
 D_ECT, T_ECT, D_HT = 1024, 512, 4096
 KERNELS = ("laplace", "fourier", "bessel")
 FP64_SAMPLE_DIRS = 128
+# DRAM bytes (read + write) per image of one FP32C hybrid launch, from the ncu capture of
+# the 8-image case in profiles/k_ht_f32_8x2048_grf.md (the tables are read once per work
+# item, so the traffic grows with the number of images)
+HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.1e6 + 4.6e6) / 8, "ht_fourier": (95.0e6 + 5.1e6) / 8,
+                           "ht_bessel": (98.0e6 + 4.4e6) / 8}
 
 
 def make_images(count: int, side: int):
@@ -281,7 +286,8 @@ def run_gpu(args):
         achieved = term_rate * fp32_ops[nm] / 1e12
         peak = lane_ops / 1e12
         roof = {"kernel": "k_ht_f32<" + nm[3:] + ">", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tlane-ops/s (FP32 pipe)", "frac": achieved / peak, "traffic": None,
+                "unit": "Tlane-ops/s (FP32 pipe)", "frac": achieved / peak,
+                "traffic": HT_DRAM_BYTES_PER_IMAGE[nm] * n_img,
                 "terms_per_s": term_rate, "fp32_lane_ops_per_term": fp32_ops[nm],
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (recipe unit counts)"}
 
@@ -297,10 +303,13 @@ def run_gpu(args):
         "ect_dirs_per_s": n_img * D_ECT * world / (ph_ms[1] / 1e3),
         "ect_updates_per_s": ect_updates / (ph_ms[1] / 1e3),
         "extraction_gbs": ext_bytes / (ph_ms[0] / 1e3) / 1e9,
+        "extraction_hbm_frac": ext_bytes / (ph_ms[0] / 1e3) / 1e9 / hbm,
         "hybrid_fp32c_evals_per_s": {k: terms / (ph_ms[2 + i] / 1e3) for i, k in enumerate(KERNELS)},
         "hybrid_fp64_evals_per_s": {k: fp64[k]["evals_per_s"] for k in KERNELS},
         "fp32c_over_fp64_speedup": {k: fp32_s[k]["evals_per_s"] / fp64[k]["evals_per_s"] for k in KERNELS},
         "fp32c_rel_err_vs_fp64": acc,
+        "fp32c_rel_err_norm": "max |FP32C - FP64| / max |FP64| over all sampled outputs; the tests bound the "
+                              "per-direction error normalised by sum |Delta kappa-bar| at 1e-6",
         "fp64_sample": f"{FP64_SAMPLE_DIRS} of {D_HT} directions, all images",
         "work": {"hybrid_terms_per_kernel": terms, "ect_updates": ect_updates, "lower_entries": n_lower,
                  "algorithmic_extraction_bytes": ext_bytes},
