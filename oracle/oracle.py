@@ -42,7 +42,7 @@ __all__ = [
     "vertex_coords", "orthant_of", "partner", "lower_star_values", "delta_values",
     "CriticalTables", "critical_tables", "euler_characteristic", "thresholds",
     "dot_products", "vertex_positions", "ect_exact", "ect_eval", "ect_values",
-    "radon_values", "ect_grid", "radon_grid",
+    "radon_values", "radon_exact", "radon_exact_eval", "ect_grid", "radon_grid",
     "radon_grid_lemma", "KERNELS", "hybrid_transform", "hybrid_transform_grad",
 ]
 
@@ -334,6 +334,50 @@ def radon_values(tab: CriticalTables, xi, t) -> np.ndarray:
     xi = np.asarray(xi, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
     return ect_values(tab, xi, t) + ect_values(tab, -xi, -t) - tab.chi
+
+
+def radon_exact(tab: CriticalTables, xi):
+    """Exact representation (T', E') of the Radon transform between critical values
+    (Section 4.3, Appendix A.2: the sorted "ordinary" critical values and the cumulative
+    sums of their values).
+
+    T' holds the distinct dot products of the points of the table Delta_eps, eps = eps^xi
+    (for a sign vector outside the stored half, the partner's table with the sign
+    flipped), ascending; E' the cumulative sums of Delta_eps with equal dot products
+    merged.  For every t that is not a dot product of a critical point,
+    R(xi, t) = E' at the largest T' < t (0 if none).  E' is the negative of the printed
+    E' of Appendix A.2, whose values are Delta^ord = -Delta_eps.
+    """
+    n = tab.n
+    half = 1 << (n - 1)
+    o = orthant_of(xi)
+    r, sg = (o, 1) if o < half else (partner(o, n), -1)
+    s = dot_products(xi, tab.delta_idx[r], tab.m)
+    order = np.argsort(s, kind="stable")
+    s_sorted = s[order]
+    v_sorted = sg * tab.delta_val[r][order]
+    Tv, first = np.unique(s_sorted, return_index=True)
+    merged = np.add.reduceat(v_sorted, first) if len(first) else np.zeros(0, np.int64)
+    return Tv, np.cumsum(merged)
+
+
+def radon_exact_eval(T_lw, E_lw, T_ord, E_ord, t) -> np.ndarray:
+    """R(xi, t) at arbitrary t from the two exact representations (Appendix A.3).
+
+    Splitting the level set as in radon_values, with sum_v Delta^-_{-eps}(v) = chi:
+      R(xi, t) = sum_{s_v < t} Delta_eps(v) + sum_{s_v = t} Delta^-_eps(v),
+    i.e. E' at the largest T' < t, plus the jump of E at t when t is one of the lower
+    critical values T ((T, E) = ect_exact).
+    """
+    t = np.asarray(t, dtype=np.float64)
+    i = np.searchsorted(T_ord, t, side="left")                 # number of T' < t
+    below = np.concatenate([np.zeros(1, np.int64), np.asarray(E_ord, np.int64)])[i]
+    T_lw = np.asarray(T_lw, dtype=np.float64)
+    E0 = np.concatenate([np.zeros(1, np.int64), np.asarray(E_lw, np.int64)])   # E0[k] = E before T[k]
+    k_le = np.searchsorted(T_lw, t, side="right")             # number of T <= t
+    k_lt = np.searchsorted(T_lw, t, side="left")              # number of T < t
+    jump = E0[k_le] - E0[k_lt]                                 # the jump at t, 0 if t is not in T
+    return below + jump
 
 
 def ect_grid(tab: CriticalTables, dirs, a: float, b: float, T: int) -> np.ndarray:

@@ -94,6 +94,24 @@ def test_worked_example_radon_and_ht(golden):
     assert abs(val[0] - exact) < 1e-13
 
 
+def test_worked_example_radon_exact(golden):
+    img = np.array(golden["image"])
+    tab = O.critical_tables(img)
+    xi = np.array(golden["ect"]["xi"])
+    rd = golden["radon"]
+    Tp, Ep = O.radon_exact(tab, xi)
+    # the two -2/3 dot products differ by one ulp: merge within 1e-12 as for the ECT
+    gT, gE = [], []
+    for t, e in zip(Tp, Ep):
+        if gT and abs(t - gT[-1]) < 1e-12:
+            gE[-1] = e
+        else:
+            gT.append(t)
+            gE.append(e)
+    np.testing.assert_allclose(gT, rd["T_ord"], atol=1e-12)
+    assert [int(e) for e in gE] == [-e for e in rd["E_prime_printed"]]
+
+
 # ---------------------------------------------------------------- brute force
 
 def _tiny_images():
@@ -149,6 +167,10 @@ def test_transforms_against_cells(img):
         t = np.concatenate([us, (us[:-1] + us[1:]) / 2, [us[0] - 1, us[-1] + 1]])
         np.testing.assert_array_equal(O.ect_values(tab, xi, t), B.ect_brute(img, xi, t))
         np.testing.assert_array_equal(O.radon_values(tab, xi, t), B.radon_brute(img, xi, t))
+        # the two exact representations (Appendix A.2 / A.3) give the same values
+        Tl, El = O.ect_exact(tab, xi)
+        Tp, Ep = O.radon_exact(tab, xi)
+        np.testing.assert_array_equal(O.radon_exact_eval(Tl, El, Tp, Ep, t), B.radon_brute(img, xi, t))
         assert int(O.ect_values(tab, xi, [np.inf])[0]) == chi
     # grid form, with a grid built to hit vertex dot products exactly
     for xi in dirs[:4]:
