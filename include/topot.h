@@ -170,6 +170,48 @@ TOPOT_API topot_status radon(const topot_tables* t, const double* d_dirs, int D,
                    double t_min, double t_max, int T, int32_t* d_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Exact representations and evaluation at arbitrary thresholds
+ * (Section 4.3; Appendix A.2 computation, A.3 evaluation)
+ * ---------------------------------------------------------------------------
+ * One representation per image b and direction d (segment b * D + d), eps = eps^xi_d:
+ *   kind 0: (T, E) of t -> ECT(xi, t).  T = the distinct dot products <xi, x(v)> (the
+ *           canonical FP64 dot product) of the points of the lower table Delta^-_eps,
+ *           ascending; E = the cumulative sums of their values, equal dot products
+ *           merged.  ECT(xi, t) = E at the largest T <= t, 0 if none.
+ *   kind 1: (T', E') the same from the table Delta_eps (= -Delta^ord of the paper, so
+ *           E' is the negative of the printed E').  R(xi, t) = E' at the largest T' < t
+ *           for every t that is not a critical value.
+ * d_T [B][D][cap] FP64, d_E [B][D][cap] int32: entries 0 .. d_len[b][D]-1 of each
+ * segment are written, the rest left as they are; d_len [B][D] int64.  cap must be at
+ * least the largest table the kind can select (tables_info: n_lower for kind 0,
+ * n_delta for kind 1), else INVALID_ARG.  The handle must have been synchronised
+ * (tables_sync).  Allocates in the handle's workspace (24 B per slot); asynchronous.
+ * Errors: INVALID_ARG; OVERFLOW when a sum of |values| of a selectable table reaches
+ * 2^31; OOM when the workspace cannot grow. */
+TOPOT_API topot_status exact_representation(const topot_tables* t, int kind, const double* d_dirs, int D,
+                                            int per_image_dirs, int64_t cap, double* d_T, int32_t* d_E,
+                                            int64_t* d_len, void* stream);
+
+/* ECT(xi, t_q) from kind-0 representations: d_out[r][q] = E at the largest T <= t_q of
+ * representation r (0 if none), r < nrep = B * D, q < Q; d_t [Q] FP64 (not NaN).
+ * Arrays as written by exact_representation with the same cap.  INVALID_ARG on bad
+ * sizes or NULL pointers. */
+TOPOT_API topot_status ect_exact_eval(int nrep, int64_t cap, const double* d_T, const int32_t* d_E,
+                                      const int64_t* d_len, const double* d_t, int Q, int32_t* d_out,
+                                      void* stream);
+
+/* R(xi, t_q) at every t_q from a kind-0 (cap, d_T, d_E, d_len) and a kind-1 (cap_ord,
+ * d_Tord, d_Eord, d_len_ord) representation of the same images and directions:
+ *   R(xi, t) = sum_{s_v < t} Delta_eps(v) + sum_{s_v = t} Delta^-_eps(v)
+ *            = E' at the largest T' < t  +  the jump of E at t (0 if t is not in T),
+ * the level set {xi = t} split as {xi <= t} + {xi >= t} - everything (additivity of the
+ * Euler integral).  d_out [nrep][Q] int32. */
+TOPOT_API topot_status radon_exact_eval(int nrep, int64_t cap, const double* d_T, const int32_t* d_E,
+                                        const int64_t* d_len, int64_t cap_ord, const double* d_Tord,
+                                        const int32_t* d_Eord, const int64_t* d_len_ord, const double* d_t, int Q,
+                                        int32_t* d_out, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Hybrid transforms (Section 2.2; closed form and sign of Lemma 3.1)
  * ---------------------------------------------------------------------------
  *   HT(xi) = - sum_v Delta^ord_eps(v) kbar(<xi, v>) = sum_v Delta_eps(v) kbar(<xi, v>)

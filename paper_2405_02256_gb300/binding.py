@@ -26,7 +26,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "
 API_SYMBOLS = (
     "build_critical_tables", "tables_create", "tables_build", "tables_sync", "tables_info",
     "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
-    "hybrid_transform_grad", "hybrid_transform_noalloc", "topot_last_error",
+    "hybrid_transform_grad", "hybrid_transform_noalloc", "exact_representation", "ect_exact_eval",
+    "radon_exact_eval", "topot_last_error",
 )
 
 
@@ -71,6 +72,9 @@ def load(path: str = LIB_PATH):
         "hybrid_transform": [vp, i32, i32, vp, i32, i32, vp, vp],
         "hybrid_transform_grad": [vp, i32, i32, vp, i32, i32, vp, vp, vp],
         "hybrid_transform_noalloc": [vp, i32, i32, vp, i32, i32, vp, vp],
+        "exact_representation": [vp, i32, vp, i32, i32, ctypes.c_int64, vp, vp, vp, vp],
+        "ect_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
+        "radon_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -257,6 +261,76 @@ def radon(tables: Tables, dirs: torch.Tensor, t_min: float, t_max: float, T: int
         out = torch.empty((tables.B, D, T), dtype=torch.int32, device=dirs.device)
     _check(L.radon(tables.handle, _ptr(dirs), D, per, float(t_min), float(t_max), int(T), _ptr(out),
                    _stream(stream)))
+    return out
+
+
+class ExactRep:
+    """Exact representations of one kind for every image and direction (device tensors):
+    T float64 [B, D, cap], E int32 [B, D, cap], length int64 [B, D]; entries past the
+    length of a segment are unspecified."""
+
+    def __init__(self, kind: int, T: torch.Tensor, E: torch.Tensor, length: torch.Tensor):
+        self.kind, self.T, self.E, self.length = kind, T, E, length
+
+    @property
+    def cap(self) -> int:
+        return self.T.shape[-1]
+
+    def segment(self, b: int, d: int):
+        """(T, E) of image b and direction d as numpy arrays."""
+        n = int(self.length[b, d])
+        return self.T[b, d, :n].cpu().numpy(), self.E[b, d, :n].cpu().numpy()
+
+
+def exact_representation(tables: Tables, kind: int, dirs: torch.Tensor, cap: int = None, stream=None) -> ExactRep:
+    """Kind 0: (T, E) of t -> ECT(xi_d, t); kind 1: (T', E') of the Radon transform between
+    critical values, for every image and direction (Section 4.3, Appendix A.2)."""
+    L = load()
+    dirs, D, per = _dirs(dirs, tables.n, tables.B)
+    if cap is None:
+        cap = 1
+        for b in range(tables.B):
+            for o in range(1 << tables.n):
+                nl, nd, _ = tables.info(b, o)
+                cap = max(cap, nl if kind == 0 else nd)
+    T = torch.empty((tables.B, D, cap), dtype=torch.float64, device=dirs.device)
+    E = torch.empty((tables.B, D, cap), dtype=torch.int32, device=dirs.device)
+    n = torch.empty((tables.B, D), dtype=torch.int64, device=dirs.device)
+    _check(L.exact_representation(tables.handle, int(kind), _ptr(dirs), D, per, int(cap), _ptr(T), _ptr(E),
+                                  _ptr(n), _stream(stream)))
+    return ExactRep(kind, T, E, n)
+
+
+def _queries(t, device):
+    t = torch.as_tensor(t, dtype=torch.float64, device=device).reshape(-1).contiguous()
+    if t.numel() < 1:
+        raise ValueError("need at least one threshold")
+    return t
+
+
+def ect_exact_eval(rep: ExactRep, t, stream=None) -> torch.Tensor:
+    """ECT(xi_d, t_q) from kind-0 representations (Appendix A.3): int32 [B, D, Q]."""
+    if rep.kind != 0:
+        raise ValueError("ect_exact_eval needs a kind-0 representation")
+    B, D, cap = rep.T.shape
+    t = _queries(t, rep.T.device)
+    out = torch.empty((B, D, t.numel()), dtype=torch.int32, device=rep.T.device)
+    _check(load().ect_exact_eval(B * D, cap, _ptr(rep.T), _ptr(rep.E), _ptr(rep.length), _ptr(t), t.numel(),
+                                 _ptr(out), _stream(stream)))
+    return out
+
+
+def radon_exact_eval(rep_lower: ExactRep, rep_ord: ExactRep, t, stream=None) -> torch.Tensor:
+    """R(xi_d, t_q) at arbitrary t_q from a kind-0 and a kind-1 representation of the same
+    images and directions: int32 [B, D, Q]."""
+    if rep_lower.kind != 0 or rep_ord.kind != 1 or rep_lower.T.shape[:2] != rep_ord.T.shape[:2]:
+        raise ValueError("radon_exact_eval needs kind-0 and kind-1 representations of the same directions")
+    B, D, cap = rep_lower.T.shape
+    t = _queries(t, rep_lower.T.device)
+    out = torch.empty((B, D, t.numel()), dtype=torch.int32, device=rep_lower.T.device)
+    _check(load().radon_exact_eval(B * D, cap, _ptr(rep_lower.T), _ptr(rep_lower.E), _ptr(rep_lower.length),
+                                   rep_ord.cap, _ptr(rep_ord.T), _ptr(rep_ord.E), _ptr(rep_ord.length), _ptr(t),
+                                   t.numel(), _ptr(out), _stream(stream)))
     return out
 
 

@@ -719,3 +719,98 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
 }
 
 }  // extern "C"
+
+// ---- exact representations (Section 4.3; Appendix A.2 / A.3) ----------------------------
+
+namespace topot {
+cudaError_t launch_exact(int n, bool u8, ExactArgs a, long long max_n, int sm_count, cudaStream_t st);
+cudaError_t launch_ect_exact_eval(int nseg, long long cap, const double* T, const int32_t* E, const long long* len,
+                                  const double* t, int Q, int32_t* out, int sm_count, cudaStream_t st);
+cudaError_t launch_radon_exact_eval(int nseg, long long cap, const double* Tl, const int32_t* El,
+                                    const long long* lenl, long long cap_o, const double* To, const int32_t* Eo,
+                                    const long long* leno, const double* t, int Q, int32_t* out, int sm_count,
+                                    cudaStream_t st);
+}  // namespace topot
+
+extern "C" {
+
+topot_status exact_representation(const topot_tables* tc, int kind, const double* d_dirs, int D, int per_image_dirs,
+                                  int64_t cap, double* d_T, int32_t* d_E, int64_t* d_len, void* stream) {
+    topot_tables* t = const_cast<topot_tables*>(tc);
+    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_T || !d_E || !d_len || (kind != 0 && kind != 1))
+        return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: bad handle, kind, directions or output");
+    if (!t->host_valid) return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: call tables_sync first");
+    const long long nseg = (long long)t->B * D;
+    if (cap < 1 || nseg > (1ll << 31) - 1 || cap > (1ll << 31) - 1)
+        return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: cap or B * D out of range");
+    // the largest table the directions can select, and the int32 bound of the sums
+    long long max_n = 0;
+    for (int b = 0; b < t->B; ++b) {
+        const long long* c = t->h_seg_count.data() + (size_t)b * t->S;
+        const long long* a = t->h_absum.data() + (size_t)b * t->NO;
+        for (int o = 0; o < t->NO; ++o) {
+            const int r = (o & (t->NO >> 1)) ? (o ^ (t->NO - 1)) : o;
+            max_n = std::max(max_n, kind == 0 ? c[o] : c[t->NO + r]);
+            const long long bound = kind == 0 ? a[o] : a[o] + a[o ^ (t->NO - 1)];
+            if (bound >= (1ll << 31))
+                return fail(TOPOT_ERR_OVERFLOW, "exact_representation: sum |Delta^-| too large for int32 sums");
+        }
+    }
+    if (max_n > cap)
+        return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: cap " + std::to_string(cap) +
+                                               " < largest table " + std::to_string(max_n));
+    const size_t slots = (size_t)nseg * (size_t)cap;
+    const size_t need = 2 * slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * (size_t)nseg + 8 * 256;
+    topot_status s = ensure_ws(t, need);
+    if (s != TOPOT_OK) return s;
+    Carver cv{reinterpret_cast<char*>(t->ws)};
+    ExactArgs a{};
+    a.t = t->dev();
+    a.dirs = d_dirs;
+    a.D = D;
+    a.per_image = per_image_dirs;
+    a.kind = kind;
+    a.nseg = (int)nseg;
+    a.cap = cap;
+    a.key[0] = cv.take<unsigned long long>(slots);
+    a.key[1] = cv.take<unsigned long long>(slots);
+    a.val[0] = cv.take<int>(slots);
+    a.val[1] = cv.take<int>(slots);
+    a.cnt = cv.take<int>((size_t)nseg);
+    a.T = d_T;
+    a.E = d_E;
+    a.len = reinterpret_cast<long long*>(d_len);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    TOPOT_CUDA(cudaMemsetAsync(d_len, 0, sizeof(int64_t) * (size_t)nseg, st));
+    TOPOT_CUDA(launch_exact(t->n, t->dtype == TOPOT_U8, a, max_n, t->sm_count, st));
+    return TOPOT_OK;
+}
+
+topot_status ect_exact_eval(int nrep, int64_t cap, const double* d_T, const int32_t* d_E, const int64_t* d_len,
+                            const double* d_t, int Q, int32_t* d_out, void* stream) {
+    if (nrep < 1 || cap < 1 || Q < 1 || !d_T || !d_E || !d_len || !d_t || !d_out)
+        return fail(TOPOT_ERR_INVALID_ARG, "ect_exact_eval: bad sizes or NULL pointer");
+    int dev = 0, sms = 0;
+    TOPOT_CUDA(cudaGetDevice(&dev));
+    TOPOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TOPOT_CUDA(launch_ect_exact_eval(nrep, cap, d_T, d_E, reinterpret_cast<const long long*>(d_len), d_t, Q, d_out,
+                                     sms, reinterpret_cast<cudaStream_t>(stream)));
+    return TOPOT_OK;
+}
+
+topot_status radon_exact_eval(int nrep, int64_t cap, const double* d_T, const int32_t* d_E, const int64_t* d_len,
+                              int64_t cap_ord, const double* d_Tord, const int32_t* d_Eord, const int64_t* d_len_ord,
+                              const double* d_t, int Q, int32_t* d_out, void* stream) {
+    if (nrep < 1 || cap < 1 || cap_ord < 1 || Q < 1 || !d_T || !d_E || !d_len || !d_Tord || !d_Eord || !d_len_ord || !d_t ||
+        !d_out)
+        return fail(TOPOT_ERR_INVALID_ARG, "radon_exact_eval: bad sizes or NULL pointer");
+    int dev = 0, sms = 0;
+    TOPOT_CUDA(cudaGetDevice(&dev));
+    TOPOT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TOPOT_CUDA(launch_radon_exact_eval(nrep, cap, d_T, d_E, reinterpret_cast<const long long*>(d_len), cap_ord,
+                                       d_Tord, d_Eord, reinterpret_cast<const long long*>(d_len_ord), d_t, Q, d_out,
+                                       sms, reinterpret_cast<cudaStream_t>(stream)));
+    return TOPOT_OK;
+}
+
+}  // extern "C"

@@ -98,6 +98,23 @@ struct ExtractArgs {
     int stage_bytes;                  // 8-bit kernel: staged bytes per tile (max over images)
 };
 
+// Arguments of the exact-representation kernels (one segment per image and direction).
+struct ExactArgs {
+    TablesDev t;
+    const double* dirs;
+    int D;
+    int per_image;
+    int kind;
+    int nseg;                        // B * D
+    long long cap;                   // slots per segment
+    unsigned long long* key[2];      // [nseg][cap], ping-pong
+    int* val[2];
+    int* cnt;                        // [nseg] entries per segment
+    double* T;                       // [nseg][cap]
+    int32_t* E;
+    long long* len;                  // [nseg]
+};
+
 // Look-back status words of the extraction kernels: 2-bit flag + 62-bit count.
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate available
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix available
