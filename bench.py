@@ -385,6 +385,31 @@ def extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, de
         ms = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, dirs_ht, gout, "fp32c", out=g), reps=1)
         adj[k] = {"ms": ms, "terms_per_s": terms / (ms / 1e3)}
     rows["adjoint_2d"] = {"workload": "same tables; 4096 dirs, d/dxi of sum_b,d HT", **adj}
+
+    # f1: exact representations (T, E) and (T', E') at 4 directions per image, and their
+    # evaluation at 4096 arbitrary thresholds
+    tabs.sync()                                   # sizes on the host (the step rebuilt the tables)
+    d4 = dirs_ht[:4].contiguous()
+    o4 = _orthants(dirs_ht_h[:4])
+    ent0 = int(sum(nl[:, o].sum() for o in o4))
+    ent1 = int(sum(nd[:, o if o < 2 else o ^ 3].sum() for o in o4))
+    cap0 = int(nl.max())
+    cap1 = int(nd.max())
+    reps = {}
+    ms0 = _time_cuda(lambda: reps.__setitem__(0, tb.exact_representation(tabs, 0, d4, cap=cap0)), reps=2)
+    ms1 = _time_cuda(lambda: reps.__setitem__(1, tb.exact_representation(tabs, 1, d4, cap=cap1)), reps=2)
+    q = torch.linspace(-R2, R2, 4096, dtype=torch.float64, device=dev)
+    ms_e = _time_cuda(lambda: tb.ect_exact_eval(reps[0], q))
+    ms_r = _time_cuda(lambda: tb.radon_exact_eval(reps[0], reps[1], q))
+    rows["exact_2d"] = {
+        "workload": f"same {n_img} x 2048^2 tables; exact representations at 4 hybrid directions per image "
+                    "(sort of the FP64 dot products, ties merged), evaluated at 4096 thresholds",
+        "ect_rep_ms": ms0, "ect_rep_entries_per_s": ent0 / (ms0 / 1e3),
+        "radon_rep_ms": ms1, "radon_rep_entries_per_s": ent1 / (ms1 / 1e3),
+        "ect_eval_ms": ms_e, "radon_eval_ms": ms_r,
+        "evals_per_s": n_img * 4 * 4096 / (ms_e / 1e3),
+    }
+    del reps
     return rows
 
 
