@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by the test-suite, never by the product path.
 
 It enumerates every cell of the weighted cubical complex of an image (vertex
-construction, Section 5) and evaluates the transforms from their definitions
+construction, Section 5; or top-dimensional construction, Section 4.1) and evaluates
+the transforms from their definitions
 (Section 2.2) via the per-cell formulas of Lemma 2.1 with the signs restored:
 
 * ECT(xi, t)  = sum_P (-1)^dim P phi(P) [max_P xi <= t]
@@ -51,11 +52,57 @@ def cells(img: np.ndarray):
     return out
 
 
-def vertex_dots(img: np.ndarray, xi) -> np.ndarray:
-    """<xi, x(v)> for every vertex, in linear order, canonical rounding."""
+def cells_top(img: np.ndarray):
+    """All cells of the top-dimensional construction (Section 4.1): every face of every
+    pixel, valued by the minimum over the pixels containing it; vertices are indices of
+    the (m_k + 1)^n grid of pixel corners.  List of (dim, phi, vertex linear indices)."""
+    img = np.asarray(img).astype(np.int64)
+    n = img.ndim
+    m = tuple(reversed(img.shape))            # pixels per paper axis, m_0 fastest
+    mv = tuple(mk + 1 for mk in m)
+    strides = [1]
+    for k in range(1, n):
+        strides.append(strides[-1] * mv[k - 1])
+    flat = img.reshape(-1)
+    pstrides = [1]
+    for k in range(1, n):
+        pstrides.append(pstrides[-1] * m[k - 1])
+    value = {}
+    for p in product(*[range(mk) for mk in m]):
+        phi = int(flat[sum(p[k] * pstrides[k] for k in range(n))])
+        for S in product((0, 1), repeat=n):
+            for b in product((0, 1), repeat=n):
+                if any(S[k] and b[k] for k in range(n)):
+                    continue
+                key = (tuple(p[k] + b[k] for k in range(n)), S)
+                value[key] = min(value.get(key, phi), phi)
+    out = []
+    for (base, S), phi in value.items():
+        verts = []
+        for g in product((0, 1), repeat=n):
+            if any(g[k] > S[k] for k in range(n)):
+                continue
+            verts.append(sum((base[k] + g[k]) * strides[k] for k in range(n)))
+        out.append((sum(S), phi, np.array(verts, dtype=np.int64)))
+    return out
+
+
+def _complex(img, construction):
+    """(cells, numpy shape of the vertex grid) of a construction."""
+    img = np.asarray(img)
+    if construction == "vertex":
+        return cells(img), img.shape
+    if construction == "top":
+        return cells_top(img), tuple(s + 1 for s in img.shape)
+    raise ValueError("construction must be 'vertex' or 'top'")
+
+
+def vertex_dots(img: np.ndarray, xi, shape=None) -> np.ndarray:
+    """<xi, x(v)> for every vertex, in linear order, canonical rounding.  The vertex grid
+    has the numpy shape ``shape`` (default: the image's own, vertex construction)."""
     img = np.asarray(img)
     n = img.ndim
-    m = tuple(reversed(img.shape))
+    m = tuple(reversed(shape if shape is not None else img.shape))
     N = int(np.prod(m))
     idx = np.arange(N, dtype=np.int64)
     s = None
@@ -68,11 +115,12 @@ def vertex_dots(img: np.ndarray, xi) -> np.ndarray:
     return s
 
 
-def ect_brute(img, xi, t) -> np.ndarray:
-    s = vertex_dots(img, xi)
+def ect_brute(img, xi, t, construction: str = "vertex") -> np.ndarray:
+    cl, shape = _complex(img, construction)
+    s = vertex_dots(img, xi, shape)
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     out = np.zeros(t.shape, dtype=np.int64)
-    for dim, phi, verts in cells(img):
+    for dim, phi, verts in cl:
         if phi == 0:
             continue
         hi = s[verts].max()
@@ -81,11 +129,12 @@ def ect_brute(img, xi, t) -> np.ndarray:
     return out
 
 
-def radon_brute(img, xi, t) -> np.ndarray:
-    s = vertex_dots(img, xi)
+def radon_brute(img, xi, t, construction: str = "vertex") -> np.ndarray:
+    cl, shape = _complex(img, construction)
+    s = vertex_dots(img, xi, shape)
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     out = np.zeros(t.shape, dtype=np.int64)
-    for dim, phi, verts in cells(img):
+    for dim, phi, verts in cl:
         if phi == 0:
             continue
         lo, hi = s[verts].min(), s[verts].max()
@@ -127,7 +176,7 @@ def lower_star_brute(img, xi) -> np.ndarray:
     return out
 
 
-def ht_by_quadrature(img, xi, kappa, order: int = 12) -> complex:
+def ht_by_quadrature(img, xi, kappa, order: int = 12, construction: str = "vertex") -> complex:
     """HT in the paper's sign convention, -int kappa(t) R(xi, t) dt, by quadrature.
 
     R(xi, .) is constant on the open intervals between consecutive distinct vertex
@@ -136,12 +185,13 @@ def ht_by_quadrature(img, xi, kappa, order: int = 12) -> complex:
     with an ``order``-point Gauss-Legendre rule.  Needs no primitive of kappa.
     """
     xi = np.asarray(xi, dtype=np.float64)
-    s = np.unique(vertex_dots(img, xi))
+    shape = _complex(img, construction)[1]
+    s = np.unique(vertex_dots(img, xi, shape))
     if len(s) < 2:
         return 0.0
     mids = 0.5 * (s[:-1] + s[1:])
-    chi = int(ect_brute(img, xi, np.array([np.inf]))[0])
-    R = ect_brute(img, xi, mids) + ect_brute(img, -xi, -mids) - chi
+    chi = int(ect_brute(img, xi, np.array([np.inf]), construction)[0])
+    R = ect_brute(img, xi, mids, construction) + ect_brute(img, -xi, -mids, construction) - chi
     nodes, weights = np.polynomial.legendre.leggauss(order)
     total = 0.0
     for lo, hi, r in zip(s[:-1], s[1:], R):

@@ -39,7 +39,7 @@ from itertools import product
 import numpy as np
 
 __all__ = [
-    "vertex_coords", "orthant_of", "partner", "lower_star_values", "delta_values",
+    "vertex_coords", "orthant_of", "partner", "lower_star_values", "lower_star_values_top", "delta_values",
     "CriticalTables", "critical_tables", "euler_characteristic", "thresholds",
     "dot_products", "vertex_positions", "ect_exact", "ect_eval", "ect_values",
     "radon_values", "radon_exact", "radon_exact_eval", "ect_grid", "radon_grid",
@@ -155,6 +155,50 @@ def lower_star_values(img: np.ndarray) -> np.ndarray:
     return out
 
 
+def lower_star_values_top(img: np.ndarray) -> np.ndarray:
+    """Delta^-_eps(v) for the top-dimensional construction (Section 4.1).
+
+    One top-dimensional cell per pixel; every lower-dimensional cell takes the minimum
+    of the values of its cofaces, i.e. of the pixels that contain it.  The vertices are
+    the corners of the pixel grid, (m_k + 1) per axis.  For the sign vector eps the
+    lower star of a corner v is made of the boxes spanned by v and v - delta (.) eps,
+    delta in {0,1}^n, as in the vertex construction.  A box lies in the pixels p with
+    p_k = v_k - 1 (eps_k = +1) or p_k = v_k (eps_k = -1) on the axes where delta_k = 1,
+    and p_k in {v_k - 1, v_k} on the others; it exists iff one of those is a pixel, and
+    its value is the minimum over them.
+
+    Returns an int64 array of shape (2^n,) + (img.shape + 1); entry [o] holds orthant o.
+    """
+    img = np.asarray(img).astype(np.int64)
+    n = img.ndim
+    shape_v = tuple(s + 1 for s in img.shape)
+    big = np.iinfo(np.int64).max // 4
+    # padded[v + g] = pixel v + g - 1 (numpy axes), g in {0,1}^n
+    padded = np.full(tuple(s + 2 for s in img.shape), big, dtype=np.int64)
+    present = np.zeros(padded.shape, dtype=bool)
+    inner = tuple(slice(1, s + 1) for s in img.shape)
+    padded[inner] = img
+    present[inner] = True
+    out = np.zeros((1 << n,) + shape_v, dtype=np.int64)
+    for o in range(1 << n):
+        eps = [(-1 if (o >> k) & 1 else 1) for k in range(n)]     # paper coordinate k
+        acc = np.zeros(shape_v, dtype=np.int64)
+        for delta in product((0, 1), repeat=n):
+            cell_min, cell_exists = None, None
+            for g in product((0, 1), repeat=n):
+                # on a spanned axis only the pixel on the side of v - eps contains the box
+                if any(delta[k] and g[k] != (0 if eps[k] == 1 else 1) for k in range(n)):
+                    continue
+                sl = tuple(slice(g[n - 1 - ax], g[n - 1 - ax] + shape_v[ax]) for ax in range(n))
+                vals, here = padded[sl], present[sl]
+                cell_min = vals if cell_min is None else np.minimum(cell_min, vals)
+                cell_exists = here if cell_exists is None else (cell_exists | here)
+            sign = -1 if (sum(delta) % 2) else 1
+            acc += sign * np.where(cell_exists, cell_min, 0)
+        out[o] = acc
+    return out
+
+
 def delta_values(lower: np.ndarray) -> np.ndarray:
     """Delta_eps = Delta^-_eps - Delta^-_{-eps} for the representative orthants.
 
@@ -193,17 +237,24 @@ class CriticalTables:
         return tuple(reversed(self.shape))
 
 
-def critical_tables(img: np.ndarray) -> CriticalTables:
+def critical_tables(img: np.ndarray, construction: str = "vertex") -> CriticalTables:
     """Preprocessing of critical points and values (Section 4.2).
 
     For every sign vector the non-zero classical values Delta^-_eps and the non-zero
     Delta_eps are stored as (points, values) arrays.  Points are linear vertex
-    indices in ascending order.
+    indices in ascending order.  construction = "vertex" (pixels are vertices, Section 5)
+    or "top" (pixels are top-dimensional cells, Section 4.1; the vertices are the
+    (m_k + 1)^n pixel corners and the tables' shape is img.shape + 1).
     """
     img = np.asarray(img)
-    low = lower_star_values(img)
+    if construction == "vertex":
+        low = lower_star_values(img)
+    elif construction == "top":
+        low = lower_star_values_top(img)
+    else:
+        raise ValueError("construction must be 'vertex' or 'top'")
     dl = delta_values(low)
-    t = CriticalTables(shape=tuple(img.shape))
+    t = CriticalTables(shape=tuple(low.shape[1:]))
     for o in range(low.shape[0]):
         flat = low[o].reshape(-1)
         idx = np.flatnonzero(flat)

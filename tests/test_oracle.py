@@ -179,6 +179,51 @@ def test_transforms_against_cells(img):
             B.ect_brute(img, xi, O.thresholds(-1.5, 1.5, 13)))
 
 
+@pytest.mark.parametrize("img", _tiny_images(), ids=lambda a: "x".join(map(str, a.shape)) + a.dtype.name)
+def test_top_construction_against_cells(img):
+    # pixels as top-dimensional cells (Section 4.1): tables on the (m_k + 1)^n corners
+    rng = np.random.default_rng(17)
+    tab = O.critical_tables(img, "top")
+    assert tab.shape == tuple(s + 1 for s in img.shape)
+    cl = B.cells_top(img)
+    chi = sum((-1) ** d * phi for d, phi, _ in cl)
+    assert tab.chi == chi
+    low = O.lower_star_values_top(img)
+    for o in range(low.shape[0]):
+        assert int(low[o].sum()) == chi
+    n = img.ndim
+    dirs = _generic_dirs(n, rng, count=1)
+    z = rng.uniform(0.3, 1.5, size=n)
+    z[0] = 0.0
+    dirs.append(z)
+    for xi in dirs:
+        s = B.vertex_dots(img, xi, tab.shape)
+        us = np.unique(s)
+        t = np.concatenate([us, (us[:-1] + us[1:]) / 2, [us[0] - 1, us[-1] + 1]])
+        np.testing.assert_array_equal(O.ect_values(tab, xi, t), B.ect_brute(img, xi, t, "top"))
+        np.testing.assert_array_equal(O.radon_values(tab, xi, t), B.radon_brute(img, xi, t, "top"))
+    xi = dirs[0]
+    for kernel, kappa in (("laplace", np.exp), ("fourier", lambda u: np.exp(-1j * u))):
+        val, norm = O.hybrid_transform(tab, kernel, [xi])
+        q = B.ht_by_quadrature(img, xi, kappa, construction="top")
+        assert abs(val[0] - q) <= 1e-9 * max(1.0, norm[0])
+
+
+def test_top_construction_constant_image():
+    # every cell of the box [0, m]^n has the value c: the complex is contractible, so
+    # ECT(xi, t) = c for t >= the smallest corner dot product and 0 below (closed form)
+    for shape in [(1, 1), (3, 5), (2, 3, 4)]:
+        img = np.full(shape, 7, dtype=np.int64)
+        tab = O.critical_tables(img, "top")
+        assert tab.chi == 7
+        rng = np.random.default_rng(len(shape))
+        for _ in range(4):
+            xi = rng.normal(size=len(shape))
+            s = B.vertex_dots(img, xi, tab.shape)
+            t = np.array([s.min() - 1e-9, s.min(), s.max(), s.max() + 1])
+            assert O.ect_values(tab, xi, t).tolist() == [0, 7, 7, 7]
+
+
 def test_radon_lemma_form_matches_identity():
     rng = np.random.default_rng(3)
     for img in _tiny_images():
