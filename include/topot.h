@@ -14,6 +14,8 @@
  *   i_0 + m_0 (i_1 + m_1 i_2).
  * - Complex: "dual"/vertex construction (Section 5): pixels are vertices, a cube
  *   exists iff all its vertices are pixels, and carries the minimum of their values.
+ *   The top-dimensional construction (TOPOT_TOP) is described at topot_construction;
+ *   with it, m_k below means the number of pixel corners, m_k + 1.
  * - Embedding (Section 4.1): x_k(i) = (2 i - (m_k - 1)) / (2 (m_k - 1)), in [-0.5, 0.5].
  * - Orthant o in [0, 2^n): bit k set <=> eps_k = -1.  The sign vector of a direction
  *   xi is eps_k = +1 if xi_k >= 0 (zero included), else -1 (Section 3, Lemma 3.2).
@@ -59,8 +61,11 @@ typedef enum {
 
 typedef enum { TOPOT_U8 = 0, TOPOT_I32 = 1 } topot_dtype;
 
-/* TOPOT_VERTEX: dual construction (Section 5).  TOPOT_TOP (one top cube per pixel,
- * Section 4.1) is not implemented: TOPOT_ERR_UNSUPPORTED. */
+/* TOPOT_VERTEX: dual construction (Section 5): pixels are vertices, a cube carries the
+ * minimum of its vertices.  TOPOT_TOP: top-dimensional construction (Section 4.1): one
+ * top cube per pixel, every lower cell carries the minimum over the pixels containing
+ * it; the vertices are the pixel corners, so the tables, the embedding and every
+ * transform live on a grid of m_k + 1 vertices per axis (m_k >= 1 pixels). */
 typedef enum { TOPOT_VERTEX = 0, TOPOT_TOP = 1 } topot_construction;
 
 /* Kernel primitives kbar of the hybrid transform (Section 2.2; Lemma 3.1):

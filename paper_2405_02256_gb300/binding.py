@@ -226,20 +226,25 @@ class Tables:
         return getattr(self, "_tuning", Tuning()).as_dict()
 
 
-def build_critical_tables(batch: ImageBatch, stream=None) -> Tables:
+CONSTRUCTIONS = {"vertex": VERTEX, "top": TOP}
+
+
+def build_critical_tables(batch: ImageBatch, construction: str = "vertex", stream=None) -> Tables:
+    """Tables of every image: construction "vertex" (pixels are vertices) or "top" (pixels
+    are top-dimensional cells; the tables live on the m_k + 1 pixel corners per axis)."""
     L = load()
     dtype = U8 if batch.pixels.dtype == torch.uint8 else I32
     h = ctypes.c_void_p()
     _check(L.build_critical_tables(_ptr(batch.pixels), dtype, batch.n, _i64(batch.shapes), _i64(batch.offsets),
-                                   batch.B, VERTEX, _stream(stream), ctypes.byref(h)))
+                                   batch.B, CONSTRUCTIONS[construction], _stream(stream), ctypes.byref(h)))
     return Tables(h, batch.n, batch.B, dtype, batch.shapes, batch.offsets)
 
 
-def tables_create(shapes, offsets, dtype=U8) -> Tables:
+def tables_create(shapes, offsets, dtype=U8, construction: str = "vertex") -> Tables:
     shapes = np.asarray(shapes, dtype=np.int64)
     h = ctypes.c_void_p()
-    _check(load().tables_create(dtype, shapes.shape[1], _i64(shapes), _i64(offsets), shapes.shape[0], VERTEX,
-                                ctypes.byref(h)))
+    _check(load().tables_create(dtype, shapes.shape[1], _i64(shapes), _i64(offsets), shapes.shape[0],
+                                CONSTRUCTIONS[construction], ctypes.byref(h)))
     return Tables(h, shapes.shape[1], shapes.shape[0], dtype, shapes, offsets)
 
 

@@ -11,7 +11,9 @@
 #include "eval_common.cuh"
 
 namespace topot {
-cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st);
+cudaError_t launch_extract(int n, topot_dtype dtype, bool top, const ExtractArgs& a, cudaStream_t st);
+cudaError_t launch_top_prepass(const void* pixels, topot_dtype dtype, int32_t* V, const TopSrc* src, int B, int n,
+                               long long max_nv, int sm_count, cudaStream_t st);
 int extract_block(int n);
 int extract_k(int n);
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
@@ -42,8 +44,13 @@ struct topot_tables {
     long long total_entries = 0;
     long long num_tiles = 0;
     int row_stride = 0, stage_rows = 0;
-    bool u8 = false;          // 8-bit batch: extraction by k_extract_u8
+    bool u8 = false;          // 8-bit batch, vertex construction: extraction by k_extract_u8
     int stage_bytes = 0;      // its staged bytes per tile (max over images)
+    bool top = false;         // top-dimensional construction: corner image, then k_extract
+    void* top_buf = nullptr;  // TopSrc[B] followed by the int32 corner images
+    TopSrc* d_top = nullptr;
+    int32_t* d_corner = nullptr;
+    long long max_nv = 0;     // largest corner image (elements)
     // device memory
     void* meta = nullptr;             // one block: img, seg_count, chi, absum, err, ticket, status
     ImgDesc* d_img = nullptr;
@@ -158,9 +165,8 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
                            topot_construction construction, topot_tables** out) {
     if (!out) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: out is NULL");
     *out = nullptr;
-    if (construction == TOPOT_TOP)
-        return fail(TOPOT_ERR_UNSUPPORTED, "tables_create: top-dimensional construction is not implemented");
-    if (construction != TOPOT_VERTEX) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad construction");
+    if (construction != TOPOT_VERTEX && construction != TOPOT_TOP)
+        return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad construction");
     if (dtype != TOPOT_U8 && dtype != TOPOT_I32) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad dtype");
     if (n != 2 && n != 3) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: n must be 2 or 3");
     if (B < 1 || !h_shapes || !h_offsets) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad image list");
@@ -178,12 +184,17 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         delete t;
         return cuda_fail(e, "tables_create: device query");
     }
-    const int elem = dtype == TOPOT_U8 ? 1 : 4;
+    const bool top = construction == TOPOT_TOP;
+    // the top construction extracts from an int32 corner image (m_k + 1 per axis)
+    const int elem = (dtype == TOPOT_U8 && !top) ? 1 : 4;
     const int pad = 16 / elem;
     const int tile_v = extract_block(n) * extract_k(n);
     const int NP = n == 3 ? 3 : 1;
     const size_t smem_budget = 96 * 1024;
-    t->u8 = dtype == TOPOT_U8;
+    t->top = top;
+    t->u8 = dtype == TOPOT_U8 && !top;
+    std::vector<TopSrc> h_top(top ? B : 0);
+    long long v_elems = 0;
     long long tiles = 0, entries = 0;
     int max_w = 1, max_r = 1;
     t->h_img.resize(B);
@@ -192,19 +203,32 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         memset(&I, 0, sizeof(I));
         long long N = 1;
         for (int k = 0; k < 3; ++k) {
-            const long long m = k < n ? h_shapes[(long long)b * n + k] : 1;
-            if (k < n && (m < 2 || m > (1 << 24))) {
+            const long long pm = k < n ? h_shapes[(long long)b * n + k] : 1;
+            // vertices per axis: the pixels (vertex construction) or the pixel corners (top)
+            const long long m = (top && k < n) ? pm + 1 : pm;
+            if (k < n && (pm < (top ? 1 : 2) || m > (1 << 24))) {
                 delete t;
-                return fail(TOPOT_ERR_INVALID_ARG, "tables_create: every axis needs 2 <= m_k <= 2^24");
+                return fail(TOPOT_ERR_INVALID_ARG, top ? "tables_create: every axis needs 1 <= m_k < 2^24 pixels"
+                                                       : "tables_create: every axis needs 2 <= m_k <= 2^24");
             }
             I.m[k] = (int)m;
             N *= m;
+            if (top) h_top[b].m[k] = (int)pm;
         }
         if (N >= (1ll << 31) || h_offsets[b] < 0) {
             delete t;
             return fail(TOPOT_ERR_INVALID_ARG, "tables_create: an image must have < 2^31 vertices and offset >= 0");
         }
-        I.offset = h_offsets[b];
+        if (top) {
+            // corner images start at multiples of 4 elements (16 bytes)
+            h_top[b].pix_offset = h_offsets[b];
+            h_top[b].v_offset = v_elems;
+            I.offset = v_elems;
+            v_elems += (N + 3) & ~3ll;
+            t->max_nv = std::max(t->max_nv, N);
+        } else {
+            I.offset = h_offsets[b];
+        }
         I.N = N;
         I.seg_base = entries;
         entries += N * t->S;
@@ -278,6 +302,21 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
     t->ticket = reinterpret_cast<unsigned*>(m + o_tic);
     t->status = reinterpret_cast<unsigned long long*>(m + o_sta);
     t->clear_bytes = meta_bytes - o_chi;
+    if (top) {
+        const size_t src_bytes = align_up(sizeof(TopSrc) * B, 256);
+        e = cudaMalloc(&t->top_buf, src_bytes + sizeof(int32_t) * (size_t)v_elems);
+        if (e != cudaSuccess) {
+            free_tables(t);
+            return cuda_fail(e, "tables_create: corner image allocation");
+        }
+        t->d_top = reinterpret_cast<TopSrc*>(t->top_buf);
+        t->d_corner = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(t->top_buf) + src_bytes);
+        e = cudaMemcpy(t->d_top, h_top.data(), sizeof(TopSrc) * B, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_tables(t);
+            return cuda_fail(e, "tables_create: corner image descriptors");
+        }
+    }
     e = cudaMemcpy(t->d_img, t->h_img.data(), sizeof(ImgDesc) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(t->seg_count, 0, o_chi - o_cnt);   // counts + error word
     if (e != cudaSuccess) {
@@ -308,10 +347,16 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     a.row_stride = t->row_stride;
     a.stage_rows = t->stage_rows;
     a.stage_bytes = t->stage_bytes;
-    if (t->u8)
+    if (t->top) {
+        TOPOT_CUDA(launch_top_prepass(d_pixels, t->dtype, t->d_corner, t->d_top, t->B, t->n, t->max_nv, t->sm_count,
+                                      st));
+        a.pixels = t->d_corner;
+        TOPOT_CUDA(launch_extract(t->n, t->dtype, true, a, st));
+    } else if (t->u8) {
         TOPOT_CUDA(launch_extract_u8(t->n, a, st));
-    else
-        TOPOT_CUDA(launch_extract(t->n, t->dtype, a, st));
+    } else {
+        TOPOT_CUDA(launch_extract(t->n, t->dtype, false, a, st));
+    }
     return TOPOT_OK;
 }
 
@@ -417,6 +462,7 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
 void free_tables(topot_tables* t) {
     if (!t) return;
     if (t->ws) cudaFree(t->ws);
+    if (t->top_buf) cudaFree(t->top_buf);
     if (t->arena_val) cudaFree(t->arena_val);
     if (t->arena_idx) cudaFree(t->arena_idx);
     if (t->meta) cudaFree(t->meta);

@@ -17,6 +17,8 @@
 //      same image (tiles are numbered by an atomic ticket, so every predecessor
 //      belongs to a block that has already started);
 //   4. adds chi = sum Delta^-_0 and sum |Delta^-_o| of the tile to per-image totals.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace topot {
@@ -71,9 +73,64 @@ __device__ __forceinline__ void lower_star(const Tin* c, int rs, int ps, int (&o
     }
 }
 
-template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
+// Lower-star values of one corner vertex for the top-dimensional construction
+// (Section 4.1: one top cell per pixel, a lower cell carries the minimum over the pixels
+// that contain it).  The extraction runs on the corner image V of shape m + 1 with
+// V(v) = pixel(v - 1) and kTopMissing outside the image, so the 2^n pixels around corner
+// v are V(v + g), g in {0,1}^n.  The box of the lower star of v for orthant o that spans
+// the axes k with delta_k = 1 (towards -eps_k) lies in the pixels with g_k = bit k of o
+// on the spanned axes and any g_k on the others; its value is their minimum, and it
+// does not exist (adds 0) when none of them is a pixel.
+template <int NDIM>
+__device__ __forceinline__ void lower_star_top(const int32_t* c, int rs, int ps, int (&out)[1 << NDIM]) {
+    constexpr int NO = 1 << NDIM;
+    int P[NO];
+#pragma unroll
+    for (int g = 0; g < NO; ++g) P[g] = c[((g >> 2) & 1) * ps + ((g >> 1) & 1) * rs + (g & 1)];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+        int acc = 0;
+#pragma unroll
+        for (int delta = 0; delta < NO; ++delta) {
+            int m = kTopMissing;
+#pragma unroll
+            for (int g = 0; g < NO; ++g)
+                if (((g ^ o) & delta) == 0) m = min(m, P[g]);
+            const int term = m == kTopMissing ? 0 : m;
+            acc += (__popc(delta) & 1) ? -term : term;
+        }
+        out[o] = acc;
+    }
+}
+
+// Corner image V of the top-dimensional construction: V(v) = pixel(v - 1) when every
+// v_k >= 1, else kTopMissing; V has m_k + 1 entries per axis.
+template <typename Tpix>
+__global__ void k_top_prepass(const Tpix* __restrict__ pix, int32_t* __restrict__ V, const TopSrc* __restrict__ src,
+                              int B, int n) {
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const TopSrc s = src[b];
+        const int M0 = s.m[0] + 1, M1 = s.m[1] + 1, M2 = n == 3 ? s.m[2] + 1 : 1;
+        const long long NV = (long long)M0 * M1 * M2;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < NV;
+             i += (long long)gridDim.x * blockDim.x) {
+            const int x = (int)(i % M0);
+            const long long r = i / M0;
+            const int y = (int)(r % M1);
+            const int z = (int)(r / M1);
+            int v = kTopMissing;
+            if (x >= 1 && y >= 1 && (n == 2 || z >= 1))
+                v = (int)pix[s.pix_offset + ((long long)(n == 3 ? z - 1 : 0) * s.m[1] + (y - 1)) * s.m[0] + (x - 1)];
+            V[s.v_offset + i] = v;
+        }
+    }
+}
+
+template <int NDIM, typename Tin, typename Tval, int BLOCK, int K, bool TOP>
 __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     using PT = PixTraits<Tin>;
+    static_assert(!TOP || sizeof(Tin) == 4, "the corner image of the top construction is int32");
+    const Tin kSent = (Tin)(TOP ? kTopMissing : PT::sentinel());   // outside the image
     constexpr int NO = 1 << NDIM;              // orthants
     constexpr int S = NO + NO / 2;             // segments
     constexpr int NW = BLOCK / 32;
@@ -144,8 +201,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
         const bool inside = zz >= 0 && zz < m2 && yy >= 0 && yy < m1;
         if (!inside) continue;
         const Tin* src = img + ((long long)zz * m1 + yy) * m0 + x0;
-        dst[PAD - 1] = x0 > 0 ? src[-1] : (Tin)PT::sentinel();
-        dst[PAD + cols] = (x0 + cols < m0) ? src[cols] : (Tin)PT::sentinel();
+        dst[PAD - 1] = x0 > 0 ? src[-1] : kSent;
+        dst[PAD + cols] = (x0 + cols < m0) ? src[cols] : kSent;
     }
     // rows outside the image, and rows whose interior is not 16-byte aligned
     for (int q = 0; q < NP * srows; ++q) {
@@ -155,7 +212,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
         Tin* dst = stage + pl * PS + rr * RS;
         const bool inside = zz >= 0 && zz < m2 && yy >= 0 && yy < m1;
         if (!inside) {
-            for (int c = tid - 1; c <= cols; c += BLOCK) dst[PAD + c] = (Tin)PT::sentinel();
+            for (int c = tid - 1; c <= cols; c += BLOCK) dst[PAD + c] = kSent;
             continue;
         }
         const Tin* src = img + ((long long)zz * m1 + yy) * m0 + x0;
@@ -207,10 +264,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
         for (int k = 0; k < K; ++k) {
             if (j0 + k < nverts) {
                 const Tin* cp = center0 + r * RS + c;
-                lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
+                if constexpr (TOP) lower_star_top<NDIM>(reinterpret_cast<const int32_t*>(cp), RS, PS, vals[k]);
+                else lower_star<NDIM, Tin>(cp, RS, PS, vals[k]);
                 if constexpr (PT::kSigned) {
                     const int a = (int)cp[0];
-                    bad_pixel |= (a >= (1 << 26)) || (a <= -(1 << 26));
+                    bad_pixel |= (!TOP || a != kTopMissing) && ((a >= (1 << 26)) || (a <= -(1 << 26)));
                 }
                 chi_acc += vals[k][0];
 #pragma unroll
@@ -336,9 +394,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
 
 // ---- host-side launch ----------------------------------------------------------------------
 
-template <int NDIM, typename Tin, typename Tval, int BLOCK, int K>
+template <int NDIM, typename Tin, typename Tval, int BLOCK, int K, bool TOP>
 static cudaError_t launch_extract_t(const ExtractArgs& a, size_t smem, cudaStream_t st) {
-    auto kern = k_extract<NDIM, Tin, Tval, BLOCK, K>;
+    auto kern = k_extract<NDIM, Tin, Tval, BLOCK, K, TOP>;
     // attributes once per instantiation, so that launches inside stream capture only launch
     static cudaError_t attr = [&] {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -365,12 +423,34 @@ size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows)
     return off + (size_t)NP * stage_rows * row_stride * elem_bytes;
 }
 
-cudaError_t launch_extract(int n, topot_dtype dtype, const ExtractArgs& a, cudaStream_t st) {
-    // 8-bit batches go to k_extract_u8 (extract_u8.cu)
-    if (dtype != TOPOT_I32) return cudaErrorInvalidValue;
+// int32 pixels (vertex construction), or the int32 corner image of the top-dimensional
+// construction of 8-bit (int16 tables) or int32 images.  8-bit images in the vertex
+// construction go to k_extract_u8 (extract_u8.cu).
+cudaError_t launch_extract(int n, topot_dtype dtype, bool top, const ExtractArgs& a, cudaStream_t st) {
     const size_t smem = extract_smem_bytes(n, 4, a.row_stride, a.stage_rows);
-    if (n == 2) return launch_extract_t<2, int32_t, int32_t, 256, 8>(a, smem, st);
-    return launch_extract_t<3, int32_t, int32_t, 256, 4>(a, smem, st);
+    if (!top) {
+        if (dtype != TOPOT_I32) return cudaErrorInvalidValue;
+        if (n == 2) return launch_extract_t<2, int32_t, int32_t, 256, 8, false>(a, smem, st);
+        return launch_extract_t<3, int32_t, int32_t, 256, 4, false>(a, smem, st);
+    }
+    if (dtype == TOPOT_U8) {
+        if (n == 2) return launch_extract_t<2, int32_t, int16_t, 256, 8, true>(a, smem, st);
+        return launch_extract_t<3, int32_t, int16_t, 256, 4, true>(a, smem, st);
+    }
+    if (n == 2) return launch_extract_t<2, int32_t, int32_t, 256, 8, true>(a, smem, st);
+    return launch_extract_t<3, int32_t, int32_t, 256, 4, true>(a, smem, st);
+}
+
+cudaError_t launch_top_prepass(const void* pixels, topot_dtype dtype, int32_t* V, const TopSrc* src, int B, int n,
+                               long long max_nv, int sm_count, cudaStream_t st) {
+    const long long per = (max_nv + 255) / 256;
+    dim3 grid((unsigned)std::max(1ll, std::min(per, (long long)std::max(1, 8 * sm_count / std::max(1, std::min(B, 65535))))),
+              (unsigned)std::min(B, 65535));
+    if (dtype == TOPOT_U8)
+        k_top_prepass<uint8_t><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(pixels), V, src, B, n);
+    else
+        k_top_prepass<int32_t><<<grid, 256, 0, st>>>(reinterpret_cast<const int32_t*>(pixels), V, src, B, n);
+    return cudaGetLastError();
 }
 
 }  // namespace topot

@@ -98,6 +98,14 @@ struct ExtractArgs {
     int stage_bytes;                  // 8-bit kernel: staged bytes per tile (max over images)
 };
 
+// Top-dimensional construction: per image, where its pixels and its corner image live.
+constexpr int kTopMissing = 0x7fffffff;   // corner-image value of a pixel outside the image
+struct TopSrc {
+    long long pix_offset;   // element offset of the pixels in the caller's buffer
+    long long v_offset;     // element offset of the corner image in the handle's buffer
+    int m[3];               // pixels per axis (m_2 = 1 for n = 2)
+};
+
 // Arguments of the exact-representation kernels (one segment per image and direction).
 struct ExactArgs {
     TablesDev t;

@@ -49,5 +49,5 @@ def test_last_error_without_gpu(lib_path):
     # n = 4 is rejected before any CUDA call
     st = L.tables_create(0, 4, shapes, offs, 1, 0, ctypes.byref(h))
     assert st == 1 and b"n must be 2 or 3" in L.topot_last_error()
-    st = L.tables_create(0, 2, shapes, offs, 1, 1, ctypes.byref(h))
-    assert st == 2   # top-dimensional construction: unsupported
+    st = L.tables_create(0, 2, shapes, offs, 1, 7, ctypes.byref(h))
+    assert st == 1 and b"construction" in L.topot_last_error()
