@@ -321,7 +321,7 @@ def run_gpu(args):
         "setup_s": setup_s,
     }
     if not args.no_extra:
-        out["rows"] = extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev)
+        out["rows"] = extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev)
         tabs.free()
         del batch
         torch.cuda.empty_cache()
@@ -359,7 +359,7 @@ def _sizes(tabs, n_img, NO):
     return nl, nd
 
 
-def extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev):
+def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev):
     """Every other row of the hot path, measured on its own workload."""
     import torch
 
@@ -410,6 +410,24 @@ def extra_rows(tabs, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, de
         "evals_per_s": n_img * 4 * 4096 / (ms_e / 1e3),
     }
     del reps
+
+    # f2: top-dimensional construction of the same images (tables on the 2049^2 pixel
+    # corners): corner-image pre-pass + extraction, then the ECT at the 1024 x 512 grid
+    ttop = tb.tables_create(batch.shapes, batch.offsets, construction="top")
+    ms_top = _time_cuda(lambda: ttop.build(batch.pixels))
+    ttop.sync()
+    ntop = _sizes(ttop, n_img, 4)
+    ent_top = int(ntop[0].sum() + ntop[1][:, :2].sum())
+    out_top = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
+    ms_top_ect = _time_cuda(lambda: tb.ect(ttop, dirs_ect, -R2, R2, T_ECT, out=out_top))
+    rows["top_2d"] = {
+        "workload": f"same {n_img} x 2048^2 images, top-dimensional construction (tables on 2049^2 corners); "
+                    "extraction, then ECT at 1024 dirs x 512 thresholds",
+        "extract_ms": ms_top, "extract_gbs": (batch.pixels.numel() + 6 * ent_top) / (ms_top / 1e3) / 1e9,
+        "ect_ms": ms_top_ect, "ect_dirs_per_s": n_img * D_ECT / (ms_top_ect / 1e3),
+    }
+    ttop.free()
+    del out_top
     return rows
 
 
