@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
     constexpr int TDT = TD * DPL;                           // directions per work item
     static_assert(DPL == 1 || TD == 32, "two directions per lane only with 32 per warp");
     extern __shared__ float4 stage[];                       // [kHistSub]
-    int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [TDT][T + 1]
+    int* hist = reinterpret_cast<int*>(stage + kHistSub);   // [T + 1][TDT]
     __shared__ long long sh_item;
     __shared__ int sh_dir[TDT];
 
@@ -138,8 +138,12 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
 #pragma unroll
             for (int k = 0; k < 3; ++k) xi[j][k] = k < NDIM ? xp[k] : 0.0;
             cf[j] = make_coef(xi[j], NDIM, I.m, P.t_min, P.t_max, T);
-            row[j] = hist + (j * TD + dl) * HS;   // lanes of directions past the tile end
-        }                                          // bin into rows nobody reads
+            // bin-major histogram [T + 1][TDT]: the 32 lanes of a warp update 32 different
+            // columns, so a lane's bank is fixed by its direction and the shared atomics of
+            // one instruction do not conflict (TD = 32); lanes of directions past the tile
+            // end bin into columns nobody reads
+            row[j] = hist + (j * TD + dl);
+        }
 
         for (int i = tid; i < TDT * HS; i += kHistBlock) hist[i] = 0;
 
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
                             const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
                             amb[k][j] = !(fabsf(u - rf) >= cf[j].delta);
                             any |= amb[k][j];
-                            if (!amb[k][j]) atomicAdd(&row[j][bin], __float_as_int(q.w));
+                            if (!amb[k][j]) atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
                         }
                     }
                     // rare: exact FP64 binning.  A per-lane branch: lane groups of one warp
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
                                     const int bin =
                                         maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u)
                                                : exact_bin<NDIM, false>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u);
-                                    atomicAdd(&row[j][bin], __float_as_int(q.w));
+                                    atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
                                 }
                             }
                         }
@@ -252,9 +256,9 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
         int32_t* out = maxbin ? out_hi : out_lo;
         const int off = maxbin ? 1 : 0;
         for (int i = tid; i < TDT * T; i += kHistBlock) {
-            const int q = i / T;
-            const int j = i - q * T;
-            const int v = hist[q * HS + j + off];
+            const int j = i / TDT;
+            const int q = i - j * TDT;
+            const int v = hist[(j + off) * TDT + q];
             const int dd = sh_dir[q];
             if (v != 0 && dd >= 0) atomicAdd(&out[((long long)b * P.D + dd) * T + j], v);
         }
