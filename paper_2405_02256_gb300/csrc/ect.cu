@@ -23,6 +23,8 @@
 // chunk is staged in shared memory as decoded lattice coordinates.  Histograms are
 // merged into the output with integer atomics: the result is exact and does not
 // depend on the order.
+#include <type_traits>
+
 #include "eval_common.cuh"
 
 namespace topot {
@@ -145,6 +147,18 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
             row[j] = hist + (j * TD + dl);
         }
 
+        // u = (s - t_min) / h of every point lies in beta +- sum_k |A_k| (m_k - 1); when that
+        // range is inside [-0.25, T - 0.75] for every direction of the block, the clamp of u
+        // before the rounding can be left out (block-uniform choice)
+        int inside = 1;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            const float S = fabsf(cf[j].a0) * (float)(I.m[0] - 1) + fabsf(cf[j].a1) * (float)(I.m[1] - 1) +
+                            fabsf(cf[j].a2) * (float)(I.m[2] - 1);
+            inside &= (cf[j].beta - S >= -0.25f) && (cf[j].beta + S <= (float)T - 0.75f);
+        }
+        const bool clamp = !__syncthreads_and(inside);
+
         for (int i = tid; i < TDT * HS; i += kHistBlock) hist[i] = 0;
 
         const long long N = t.seg_count[(long long)b * t.S + seg];
@@ -200,55 +214,66 @@ __global__ void __launch_bounds__(kHistBlock, DPL == 1 ? 2 : 1) k_hist(EvalPlan 
                 const float umax = (float)T - 0.5f;
                 // Bin from u without float->int conversions: adding 1.5 * 2^23 rounds u to
                 // an integer r (ties to even) held in the low mantissa bits.  u is clamped to
-                // [-0.5, T - 0.5] first, so the sublevel bin ceil(u) and the superlevel index
-                // floor(u) + 1 both land in [0, T].  Points within delta of a bin edge are
-                // binned exactly on a slow path, checked once per 4 points.
-                for (int e = gs; e < ge; e += 4) {
-                    bool amb[4][DPL];
-                    bool any = false;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float4 q = stage[e + k];
-#pragma unroll
-                        for (int j = 0; j < DPL; ++j) {
-                            float u;
-                            if (NDIM == 3)
-                                u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
-                            else
-                                u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
-                            const float uc = fminf(fmaxf(u, -0.5f), umax);
-                            const float f = uc + 12582912.0f;
-                            const float rf = f - 12582912.0f;
-                            const int r = __float_as_int(f) - 0x4B400000;
-                            const int bin = maxbin ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
-                            amb[k][j] = !(fabsf(u - rf) >= cf[j].delta);
-                            any |= amb[k][j];
-                            if (!amb[k][j]) atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
-                        }
-                    }
-                    // rare: exact FP64 binning.  A per-lane branch: lane groups of one warp
-                    // may run different trip counts, so no warp-wide vote may be used here.
-                    if (any) {
+                // [-0.5, T - 0.5] first (unless no point can leave that range), so the
+                // sublevel bin ceil(u) and the superlevel index floor(u) + 1 both land in
+                // [0, T].  Points within delta of a bin edge are binned exactly on a slow
+                // path, checked once per 4 points.  The clamp and the bin side are
+                // compile-time choices of the loop, taken per work item (block-uniform).
+                auto bin_round = [&](auto cl, auto mb) {
+                    constexpr bool CL = decltype(cl)::value;
+                    constexpr bool MB = decltype(mb)::value;
+                    for (int e = gs; e < ge; e += 4) {
+                        bool amb[4][DPL];
+                        bool any = false;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
+                            const float4 q = stage[e + k];
 #pragma unroll
                             for (int j = 0; j < DPL; ++j) {
-                                if (amb[k][j]) {
-                                    const float4 q = stage[e + k];
-                                    float u;
-                                    if (NDIM == 3)
-                                        u = fmaf(q.x, cf[j].a0,
-                                                 fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
-                                    else
-                                        u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
-                                    const int bin =
-                                        maxbin ? exact_bin<NDIM, true>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u)
-                                               : exact_bin<NDIM, false>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u);
-                                    atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
+                                float u;
+                                if (NDIM == 3)
+                                    u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
+                                else
+                                    u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
+                                const float uc = CL ? fminf(fmaxf(u, -0.5f), umax) : u;
+                                const float f = uc + 12582912.0f;
+                                const float rf = f - 12582912.0f;
+                                const int r = __float_as_int(f) - 0x4B400000;
+                                const int bin = MB ? (uc < rf ? r : r + 1) : (uc > rf ? r + 1 : r);
+                                amb[k][j] = !(fabsf(u - rf) >= cf[j].delta);
+                                any |= amb[k][j];
+                                if (!amb[k][j]) atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
+                            }
+                        }
+                        // rare: exact FP64 binning.  A per-lane branch: lane groups of one warp
+                        // may run different trip counts, so no warp-wide vote may be used here.
+                        if (any) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                                for (int j = 0; j < DPL; ++j) {
+                                    if (amb[k][j]) {
+                                        const float4 q = stage[e + k];
+                                        float u;
+                                        if (NDIM == 3)
+                                            u = fmaf(q.x, cf[j].a0,
+                                                     fmaf(q.y, cf[j].a1, fmaf(q.z, cf[j].a2, cf[j].beta)));
+                                        else
+                                            u = fmaf(q.x, cf[j].a0, fmaf(q.y, cf[j].a1, cf[j].beta));
+                                        const int bin = exact_bin<NDIM, MB>(q.x, q.y, q.z, xi[j], I.m, P.thr, T, u);
+                                        atomicAdd(&row[j][bin * TDT], __float_as_int(q.w));
+                                    }
                                 }
                             }
                         }
                     }
+                };
+                using T1 = std::true_type;
+                using F0 = std::false_type;
+                if (clamp) {
+                    if (maxbin) bin_round(T1{}, T1{}); else bin_round(T1{}, F0{});
+                } else {
+                    if (maxbin) bin_round(F0{}, T1{}); else bin_round(F0{}, F0{});
                 }
             }
         }
