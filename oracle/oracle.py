@@ -494,6 +494,8 @@ KERNELS = {
     "laplace": (np.exp, np.exp),
     "fourier": (lambda s: np.sin(s) + 1j * np.cos(s), lambda s: np.cos(s) - 1j * np.sin(s)),
     "bessel": (_j0, lambda s: -_j1(s)),
+    # kappa = sin, the kernel of the paper's experiments (Section 5): kbar = -cos
+    "sine": (lambda s: -np.cos(s), np.sin),
 }
 
 

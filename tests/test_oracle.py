@@ -299,6 +299,7 @@ KAPPA = {
     "laplace": np.exp,
     "fourier": lambda t: np.exp(-1j * t),
     "bessel": None,   # filled below (needs scipy)
+    "sine": np.sin,
 }
 
 
@@ -309,7 +310,7 @@ def _kappa(name):
     return KAPPA[name]
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel", "sine"])
 def test_ht_against_cells_and_quadrature(kernel):
     rng = np.random.default_rng(21)
     kbar, _ = O.KERNELS[kernel]
@@ -336,7 +337,7 @@ def test_kernel_primitives():
     assert abs(j0(2.404825557695773)) < 1e-15 and j0(0.0) == 1.0
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel", "sine"])
 def test_gradient_central_differences(kernel):
     img = synth.grf((9, 11), 2.0, seed=31)
     tab = O.critical_tables(img)
@@ -352,6 +353,19 @@ def test_gradient_central_differences(kernel):
             fm, _ = O.hybrid_transform(tab, kernel, [xi - e])
             fd = (fp[0] - fm[0]) / (2 * h)
             assert abs(fd - g[di, k]) < 1e-6 * max(1.0, abs(g[di, k]))
+
+
+def test_sine_kernel_is_minus_imag_fourier():
+    # kappa = sin against kappa = e^{-it}: kbar_sine = -cos = -Im(sin + i cos)
+    img = synth.grf((12, 13), 2.0, seed=51)
+    tab = O.critical_tables(img)
+    dirs = _generic_dirs(2, np.random.default_rng(52), count=2)
+    vs, _ = O.hybrid_transform(tab, "sine", dirs)
+    vf, _ = O.hybrid_transform(tab, "fourier", dirs)
+    np.testing.assert_allclose(vs, -vf.imag, rtol=0, atol=1e-12)
+    gs, _ = O.hybrid_transform_grad(tab, "sine", dirs)
+    gf, _ = O.hybrid_transform_grad(tab, "fourier", dirs)
+    np.testing.assert_allclose(gs, -gf.imag, rtol=0, atol=1e-12)
 
 
 def test_orthant_rule():
