@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libtopot.so")
 
 U8, I32 = 0, 1
 VERTEX, TOP = 0, 1
-KERNELS = {"laplace": 0, "fourier": 1, "bessel": 2}
+KERNELS = {"laplace": 0, "fourier": 1, "bessel": 2, "sine": 3}
 PRECISIONS = {"fp32c": 0, "fp64": 1}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "OVERFLOW", 6: "TIMEOUT"}
 

@@ -18,6 +18,8 @@
 // s - M = sum_k (|xi_k| / (m_k - 1)) q_k with integer q_k <= 0, so every FP32 exponent
 // is <= 0 (no overflow) and is a sum of non-positive terms (no cancellation).
 // FP64: the canonical FP64 dot product and library FP64 kernels, plain FP64 sums.
+#include <algorithm>
+
 #include "eval_common.cuh"
 
 namespace topot {
@@ -971,6 +973,32 @@ cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, i
     const long long rows = (long long)P.nsets * P.D;
     k_ht_adj_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part,
                                                                        gout, gdirs);
+    return cudaGetLastError();
+}
+
+// kappa = sin on the Fourier path: HT_sine = -Im HT_Fourier, and its adjoint is the
+// Fourier adjoint with output weights (0, -g).
+__global__ void k_sine_from_fourier(const double* __restrict__ f, double* __restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = -f[2 * i + 1];
+}
+
+__global__ void k_sine_gout(const double* __restrict__ g, double* __restrict__ g2, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        g2[2 * i] = 0.0;
+        g2[2 * i + 1] = -g[i];
+    }
+}
+
+cudaError_t launch_sine_from_fourier(const double* f, double* out, long long n, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::max(1ll, std::min((n + 255) / 256, 4096ll));
+    k_sine_from_fourier<<<grid, 256, 0, st>>>(f, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sine_gout(const double* g, double* g2, long long n, cudaStream_t st) {
+    const unsigned grid = (unsigned)std::max(1ll, std::min((n + 255) / 256, 4096ll));
+    k_sine_gout<<<grid, 256, 0, st>>>(g, g2, n);
     return cudaGetLastError();
 }
 

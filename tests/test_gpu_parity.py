@@ -172,7 +172,7 @@ def _ht_err(got, want, norm, kernel):
     return np.max(np.abs(got - want) / np.maximum(norm, 1e-300))
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel", "sine"])
 @pytest.mark.parametrize("precision", ["fp32c", "fp64"])
 @pytest.mark.parametrize("name", ["example4x4", "bern64", "grf150x211", "grf20x33x64", "i32_2d", "bern9x10x11"])
 def test_hybrid_transform(tb, kernel, precision, name):
@@ -210,7 +210,7 @@ def test_hybrid_transform_worked_example(tb, golden):
     assert abs(v - golden["hybrid_transform"]["value_printed"]) < 5e-4
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel", "sine"])
 @pytest.mark.parametrize("precision", ["fp32c", "fp64"])
 @pytest.mark.parametrize("per_image", [False, True])
 def test_gradient(tb, kernel, precision, per_image):
@@ -304,7 +304,7 @@ def test_rebuild_async_and_deterministic(tb):
     _check_tables(tabs, 0, imgs[0])
 
 
-@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel", "sine"])
 def test_gradient_3d(tb, kernel):
     img = synth.grf((18, 21, 24), 3.0, seed=65)
     ref = O.critical_tables(img)
