@@ -263,6 +263,15 @@ TOPOT_API topot_status hybrid_transform_noalloc(const topot_tables* t, topot_ker
                                                int D, int per_image_dirs, double* d_out,
                                                void* stream);
 
+/* Self-test of the bounded device-side waits.  Every spin of the library (extraction
+ * look-back, wait for staged pixels) gives up after a time limit, records the timeout
+ * and returns, so that a lost predecessor or copy becomes TOPOT_ERR_TIMEOUT rather than a
+ * hung GPU.  This call makes one such wait run out on purpose, limited to limit_ms
+ * (1 .. 10000): which = 0 spins on a device flag that nothing sets, which = 1 waits on an
+ * mbarrier phase that never completes (no copy is issued).  Synchronous on `stream`.
+ * Returns TOPOT_ERR_TIMEOUT when the wait ran out as designed; INVALID_ARG, CUDA. */
+TOPOT_API topot_status topot_selftest_wait(int which, int limit_ms, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 TOPOT_API const char* topot_last_error(void);
 

@@ -27,7 +27,7 @@ API_SYMBOLS = (
     "build_critical_tables", "tables_create", "tables_build", "tables_sync", "tables_info",
     "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
     "hybrid_transform_grad", "hybrid_transform_noalloc", "exact_representation", "ect_exact_eval",
-    "radon_exact_eval", "topot_last_error",
+    "radon_exact_eval", "topot_selftest_wait", "topot_last_error",
 )
 
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "exact_representation": [vp, i32, vp, i32, i32, ctypes.c_int64, vp, vp, vp, vp],
         "ect_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
         "radon_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
+        "topot_selftest_wait": [i32, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -19,6 +19,8 @@ int extract_k(int n);
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
 cudaError_t launch_extract_u8(int n, const ExtractArgs& a, cudaStream_t st);
 cudaError_t launch_sine_from_fourier(const double* f, double* out, long long n, cudaStream_t st);
+cudaError_t launch_selftest_wait(int which, unsigned long long limit_ns, unsigned long long* flag, unsigned* err,
+                                 cudaStream_t st);
 cudaError_t launch_sine_gout(const double* g, double* g2, long long n, cudaStream_t st);
 int extract_u8_threads(int n);
 int extract_u8_strip(int n);
@@ -901,6 +903,31 @@ topot_status radon_exact_eval(int nrep, int64_t cap, const double* d_T, const in
     TOPOT_CUDA(launch_radon_exact_eval(nrep, cap, d_T, d_E, reinterpret_cast<const long long*>(d_len), cap_ord,
                                        d_Tord, d_Eord, reinterpret_cast<const long long*>(d_len_ord), d_t, Q, d_out,
                                        sms, reinterpret_cast<cudaStream_t>(stream)));
+    return TOPOT_OK;
+}
+
+}  // extern "C"
+
+// ---- self-test of the bounded waits -------------------------------------------------------
+
+extern "C" {
+
+topot_status topot_selftest_wait(int which, int limit_ms, void* stream) {
+    if ((which != 0 && which != 1) || limit_ms < 1 || limit_ms > 10000)
+        return fail(TOPOT_ERR_INVALID_ARG, "topot_selftest_wait: which must be 0 or 1, limit_ms in [1, 10000]");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void* mem = nullptr;
+    TOPOT_CUDA(cudaMalloc(&mem, 256));
+    unsigned long long* flag = reinterpret_cast<unsigned long long*>(mem);
+    unsigned* err = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(mem) + 128);
+    cudaError_t e = cudaMemsetAsync(mem, 0, 256, st);
+    if (e == cudaSuccess) e = launch_selftest_wait(which, (unsigned long long)limit_ms * 1000000ull, flag, err, st);
+    unsigned h_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(mem);
+    if (e != cudaSuccess) return cuda_fail(e, "topot_selftest_wait");
+    if (h_err & kDevErrTimeout) return fail(TOPOT_ERR_TIMEOUT, "device-side wait timed out (self-test)");
     return TOPOT_OK;
 }
 

@@ -173,10 +173,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 }
 
 // Bounded wait; false (and the error bit set) if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* err) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* err,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = dev_time_ns();
-    while (dev_time_ns() - t0 < kWaitLimitNs) {
+    while (dev_time_ns() - t0 < limit_ns) {
         if (mbar_try_wait(bar, parity)) return true;
     }
     dev_set_error(err, kDevErrTimeout);
