@@ -568,13 +568,19 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
         uint32_t J[kStrip];
 #pragma unroll
         for (int k = 0; k < kStrip; ++k) J[k] = jb + ((uint32_t)k << 16);
+        // the warp's totals: segments without an entry in this warp skip the appends
+        uint32_t wt[kWords];
+#pragma unroll
+        for (int i = 0; i < kWords; ++i) wt[i] = __shfl_sync(kFull, iw[i], 31);
         const uint32_t out_u32 = smem_u32(out);
         uint32_t base = 0;
 #pragma unroll
         for (int s = 0; s < kSeg; ++s) {
             uint32_t a = out_u32 + 4u * (base + field16(ex, s));
+            if (field16(wt, s) != 0u) {
 #pragma unroll
-            for (int q = 0; q < kPairs; ++q) append_pair(a, D[s][q], J[2 * q], J[2 * q + 1]);
+                for (int q = 0; q < kPairs; ++q) append_pair(a, D[s][q], J[2 * q], J[2 * q + 1]);
+            }
             base += field16(tot, s);
         }
     }
