@@ -46,7 +46,7 @@ template <> struct U8Cfg<2> {
 template <> struct U8Cfg<3> {
     static constexpr int B = 256;
     static constexpr int STRIP = 4;
-    static constexpr int MINB = 3;      // registers <= 85
+    static constexpr int MINB = 4;      // registers <= 64 (a few spills; measured faster than 3 blocks)
 };
 
 constexpr int kPadB = 16;               // staged row interior starts 16 bytes in
