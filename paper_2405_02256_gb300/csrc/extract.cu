@@ -1,5 +1,7 @@
-// K1: critical-table extraction for int32 pixels (Section 3, Delta^-; Section 4.2,
-// preprocessing).  8-bit images and volumes use k_extract_u8 (extract_u8.cu).
+// K1: critical-table extraction for int32 pixels, and for the top-dimensional
+// construction of 8-bit and int32 images through their int32 corner image (Section 3,
+// Delta^-; Section 4.1; Section 4.2, preprocessing).  8-bit images in the vertex
+// construction use k_extract_u8 (extract_u8.cu).
 //
 // One block per tile.  A tile is a run of vertices that is contiguous in linear
 // vertex order: R full rows of one plane (m_0 <= W) or one W-wide piece of a row.
@@ -12,10 +14,11 @@
 //      Delta^-_o(v) = sum_{delta in {0,1}^n} (-1)^|delta| min(phi over box(v, v - delta (.) eps_o))
 //      from the 3^n neighbourhood (all 2^n orthants share the edge / face minima);
 //   3. compacts the non-zero values of the 2^n lower tables and of the 2^(n-1)
-//      Delta = Delta^-_r - Delta^-_{-r} tables in vertex order: warp ballots, a block
-//      scan of the per-warp counts and a decoupled look-back over the tiles of the
-//      same image (tiles are numbered by an atomic ticket, so every predecessor
-//      belongs to a block that has already started);
+//      Delta = Delta^-_r - Delta^-_{-r} tables in vertex order: each thread owns K
+//      consecutive vertices and counts its entries per table, warp-shuffle scans and a
+//      block scan of the warp totals place them, and a decoupled look-back over the
+//      tiles of the same image (tiles are numbered by an atomic ticket, so every
+//      predecessor belongs to a block that has already started) gives the tile's start;
 //   4. adds chi = sum Delta^-_0 and sum |Delta^-_o| of the tile to per-image totals.
 #include <algorithm>
 
