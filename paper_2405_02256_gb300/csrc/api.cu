@@ -575,7 +575,8 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
             if (kernel == TOPOT_LAPLACE && per_orthant >= 256) dl = 8;
         }
         if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
-        if (adjoint && dl > 2) dl = 2;
+        // adjoint: two direction pairs per lane for the one-component kernels in 2-D, else one
+        if (adjoint) dl = std::min(dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
     }
     const int tdh = 32 * dl;
     const int nk = kernel == TOPOT_FOURIER ? 2 : 1;

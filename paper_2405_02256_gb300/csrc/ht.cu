@@ -563,54 +563,60 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f64(EvalPlan P, TablesDev t, do
 // Partials per direction: LAPLACE / BESSEL: n sums  sum Delta kappa(s) x_k;
 // FOURIER: 2n sums  (sum Delta cos(s) x_k, sum Delta sin(s) x_k)  [d Re = +cos, d Im = -sin].
 
-// Packed adjoint over staged points [ws, we) for one direction pair per lane:
+// Packed adjoint over staged points [ws, we) for NPR direction pairs per lane:
 //   g_k += v kappa(z) x_k  (Fourier: g_k += v cos z x_k and g_{n+k} += v sin z x_k)
-// with x_k rebuilt from the staged integer p_k as x_k = p_k * xa_k + xb_k.  Blocks of
-// four points are summed by FMA, then added with compensation (as the forward).
-template <int NDIM, int KERNEL, int PATH>
-__device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int we, const float2 (&w)[3],
+// with x_k rebuilt from the staged integer p_k as x_k = p_k * xa_k + xb_k (shared by the
+// pairs: it depends on the point only).  Blocks of four points are summed by FMA, then
+// added with compensation (as the forward).
+template <int NDIM, int KERNEL, int PATH, int NPR>
+__device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int we, const float2 (&w)[NPR][3],
                                                     const float2 (&xa)[3], const float2 (&xb)[3],
-                                                    float2 (&s2)[(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM],
-                                                    float2 (&n2)[(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM]) {
+                                                    float2 (&s2)[NPR][(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM],
+                                                    float2 (&n2)[NPR][(KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM]) {
     constexpr int NC = (KERNEL == TOPOT_FOURIER ? 2 : 1) * NDIM;
     constexpr int BLK = 4;
     for (int e = ws; e < we; e += BLK) {
-        float2 blk[NC];
+        float2 blk[NPR][NC];
 #pragma unroll
         for (int u = 0; u < BLK; ++u) {
             const float4 qa = A[2 * (e + u)];
             const float4 qb = A[2 * (e + u) + 1];
             const float2 pc[3] = {make_float2(qa.x, qa.y), make_float2(qa.z, qa.w), make_float2(qb.x, qb.y)};
             const float2 v2 = make_float2(qb.z, qb.w);
-            float2 z = mul2(pc[0], w[0]);
-            z = fma2(pc[1], w[1], z);
-            if (NDIM == 3) z = fma2(pc[2], w[2], z);
             float2 x[3];
 #pragma unroll
             for (int k = 0; k < NDIM; ++k) x[k] = fma2(pc[k], xa[k], xb[k]);
-            float2 t[2];
-            if (KERNEL == TOPOT_LAPLACE) {
-                t[0] = mul2(v2, make_float2(ex2_approx(z.x), ex2_approx(z.y)));
-            } else if (KERNEL == TOPOT_FOURIER) {
-                const float2 ww = mul2(z, z);
-                const float2 sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
-                const float2 cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
-                t[0] = mul2(v2, cs);
-                t[1] = mul2(v2, sn);
-            } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
-                const float2 y = mul2(z, z);
-                const float2 j1 = mul2(z, PATH == 2 ? j1q_short2(y) : j1q_long2(y));
-                t[0] = mul2(make_float2(-v2.x, -v2.y), j1);
-            }
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const float2 tc = t[c / NDIM];
-                const float2 xc = x[c % NDIM];
-                blk[c] = u == 0 ? mul2(tc, xc) : fma2(tc, xc, blk[c]);
+            for (int r = 0; r < NPR; ++r) {
+                float2 z = mul2(pc[0], w[r][0]);
+                z = fma2(pc[1], w[r][1], z);
+                if (NDIM == 3) z = fma2(pc[2], w[r][2], z);
+                float2 t[2];
+                if (KERNEL == TOPOT_LAPLACE) {
+                    t[0] = mul2(v2, make_float2(ex2_approx(z.x), ex2_approx(z.y)));
+                } else if (KERNEL == TOPOT_FOURIER) {
+                    const float2 ww = mul2(z, z);
+                    const float2 sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
+                    const float2 cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
+                    t[0] = mul2(v2, cs);
+                    t[1] = mul2(v2, sn);
+                } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
+                    const float2 y = mul2(z, z);
+                    const float2 j1 = mul2(z, PATH == 2 ? j1q_short2(y) : j1q_long2(y));
+                    t[0] = mul2(make_float2(-v2.x, -v2.y), j1);
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const float2 tc = t[c / NDIM];
+                    const float2 xc = x[c % NDIM];
+                    blk[r][c] = u == 0 ? mul2(tc, xc) : fma2(tc, xc, blk[r][c]);
+                }
             }
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) kahan2_add(s2[c], n2[c], blk[c]);
+        for (int r = 0; r < NPR; ++r)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) kahan2_add(s2[r][c], n2[r][c], blk[r][c]);
     }
 }
 
@@ -654,19 +660,22 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                 mloc = fmaxf(mloc, (float)(0.5 * (fabs(hd[j].xi[0]) + fabs(hd[j].xi[1]) + fabs(hd[j].xi[2]))));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-        int path = 0;   // packed paths: as the forward, one direction pair per lane
-        if (DL == 2) {
+        int path = 0;   // packed paths: as the forward, DL / 2 direction pairs per lane
+        if (DL >= 2) {
             if (KERNEL == TOPOT_LAPLACE) path = 1;
             else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
             else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
         }
-        if constexpr (DL == 2) {
+        if constexpr (DL >= 2) {
+            constexpr int NPR = DL / 2;
             if (path != 0) {
                 const float wsc = KERNEL == TOPOT_BESSEL ? 0.5f : 1.0f;
-                float2 w[3], xa[3], xb[3];
+                float2 w[NPR][3], xa[3], xb[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    w[k] = make_float2(wsc * hd[0].w[k], wsc * hd[1].w[k]);
+#pragma unroll
+                    for (int r = 0; r < NPR; ++r)
+                        w[r][k] = make_float2(wsc * hd[2 * r].w[k], wsc * hd[2 * r + 1].w[k]);
                     const float mk1 = (float)(it.I->m[k] - 1);
                     if (KERNEL == TOPOT_LAPLACE) {   // x = sigma (q / (m - 1) + 1/2), sigma = eps_k
                         const float sg = ((it.o >> k) & 1) ? -1.0f : 1.0f;
@@ -677,9 +686,11 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                         xb[k] = make_float2(0.0f, 0.0f);
                     }
                 }
-                float2 s2[NC], n2[NC];
+                float2 s2[NPR][NC], n2[NPR][NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) s2[c] = n2[c] = make_float2(0.0f, 0.0f);
+                for (int r = 0; r < NPR; ++r)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) s2[r][c] = n2[r][c] = make_float2(0.0f, 0.0f);
                 for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
                     const int cnt = (int)min((long long)SUB, it.e_end - e0);
                     __syncthreads();
@@ -688,16 +699,18 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                     __syncthreads();
                     const int per = cnt_pad / kHtWarps;
                     const int ws = warp * per, we = ws + per;
-                    if (path == 2) ht_adj_packed_range<NDIM, KERNEL, 2>(A, ws, we, w, xa, xb, s2, n2);
-                    else ht_adj_packed_range<NDIM, KERNEL, 1>(A, ws, we, w, xa, xb, s2, n2);
+                    if (path == 2) ht_adj_packed_range<NDIM, KERNEL, 2, NPR>(A, ws, we, w, xa, xb, s2, n2);
+                    else ht_adj_packed_range<NDIM, KERNEL, 1, NPR>(A, ws, we, w, xa, xb, s2, n2);
                 }
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    acc[0][c] = s2[c].x;
-                    cmp[0][c] = -n2[c].x;
-                    acc[1][c] = s2[c].y;
-                    cmp[1][c] = -n2[c].y;
-                }
+                for (int r = 0; r < NPR; ++r)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        acc[2 * r][c] = s2[r][c].x;
+                        cmp[2 * r][c] = -n2[r][c].x;
+                        acc[2 * r + 1][c] = s2[r][c].y;
+                        cmp[2 * r + 1][c] = -n2[r][c].y;
+                    }
             }
         }
         for (long long e0 = it.e_begin; path == 0 && e0 < it.e_end; e0 += SUB) {
@@ -923,6 +936,11 @@ static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precis
         switch (dl) {
             case 1: k_ht_adj_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
             case 2: k_ht_adj_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 4:
+                if (KERNEL == TOPOT_FOURIER) return cudaErrorInvalidValue;
+                k_ht_adj_f32<NDIM, (KERNEL == TOPOT_FOURIER ? TOPOT_LAPLACE : KERNEL), 4, Tval>
+                    <<<grid, kHtBlock, 0, st>>>(P, t, part);
+                break;
             default: return cudaErrorInvalidValue;
         }
     } else {

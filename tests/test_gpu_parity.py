@@ -249,6 +249,30 @@ def test_gradient(tb, kernel, precision, per_image):
     assert np.max(np.abs(got - want) / scale) <= 2 * HT_TOL[precision]
 
 
+@pytest.mark.parametrize("dl", [1, 2, 4])
+def test_gradient_tiles(tb, dl):
+    # the adjoint at every number of directions per lane (Fourier stops at one pair)
+    img = synth.grf((90, 80), 4.0, seed=68)
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+    dirs = synth.random_2d_dirs(600, 69, 0.05, 1.0)
+    rng = np.random.default_rng(70)
+    d = torch.from_numpy(dirs).cuda()
+    for kernel in ("laplace", "fourier", "bessel"):
+        nc = 2 if kernel == "fourier" else 1
+        gout = rng.standard_normal((1, 600, 2)) if nc == 2 else rng.standard_normal((1, 600))
+        got = tb.hybrid_transform_grad(tabs, kernel, d, torch.from_numpy(gout).cuda()).cpu().numpy()
+        g, gn = O.hybrid_transform_grad(ref, kernel, dirs)
+        if kernel == "fourier":
+            want = gout[0, :, 0:1] * g.real + gout[0, :, 1:2] * g.imag
+            sc = (np.abs(gout[0, :, 0:1]) + np.abs(gout[0, :, 1:2])) * gn
+        else:
+            want = gout[0][:, None] * g
+            sc = np.abs(gout[0])[:, None] * gn
+        assert np.max(np.abs(got - want) / sc) <= 2e-6, kernel
+
+
 def test_autograd_function(tb):
     img = synth.grf((50, 40), 4.0, seed=70)
     tabs = tb.build_critical_tables(tb.pack_images([img]))
