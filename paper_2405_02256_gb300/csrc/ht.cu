@@ -595,9 +595,17 @@ __device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int
                 if (KERNEL == TOPOT_LAPLACE) {
                     t[0] = mul2(v2, make_float2(ex2_approx(z.x), ex2_approx(z.y)));
                 } else if (KERNEL == TOPOT_FOURIER) {
-                    const float2 ww = mul2(z, z);
-                    const float2 sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
-                    const float2 cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
+                    // odd points on MUFU sin/cos, even points on the polynomials: the
+                    // XU pipe takes part of the FMA pipe's load (as the forward's pairs)
+                    float2 sn, cs;
+                    if (u & 1) {
+                        sn = make_float2(__sinf(z.x), __sinf(z.y));
+                        cs = make_float2(__cosf(z.x), __cosf(z.y));
+                    } else {
+                        const float2 ww = mul2(z, z);
+                        sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
+                        cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
+                    }
                     t[0] = mul2(v2, cs);
                     t[1] = mul2(v2, sn);
                 } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
