@@ -8,8 +8,10 @@ Fourier and Bessel hybrid transforms at 4096 directions (|xi| log-uniform in
 direction sample beside it.  Inputs (268 MB) and tables (~1.4 GB) exceed the 129 MB
 L2, so no flush is needed between steps.
 
-Prints one JSON line (see the design doc for every key).  ``--impl reference`` times the
-CPU oracle instead (a bounded sample of the same workload, same metric).
+Prints one JSON line: the metric, the timed step, the roofline of the dominant kernel,
+the CPU-oracle baseline, the end-to-end rate through host buffers, the clocks seen and
+the other rows of the path.  ``--impl reference`` times the CPU oracle instead (a
+bounded sample of the same workload, same metric).
 """
 from __future__ import annotations
 
@@ -266,8 +268,9 @@ def run_gpu(args):
     # FP32 pipe: 128 lanes per SM per clock; issue: 4 schedulers x 32 lanes per SM per clock
     lane_ops = sm_count * 128 * mhz * 1e6
     # FP32-pipe lane operations per term of each hybrid kernel as written (a packed f32x2
-    # operation counts 2, MUFU operations are not counted), and issued instructions per
-    # (point, direction) update of the ECT kernel; both counted from the source, see the design doc
+    # operation counts 2, MUFU operations are not counted; the average over the MUFU and
+    # polynomial halves for Fourier), and issued instructions per (point, direction)
+    # update of the ECT kernel; both counted from the kernel source
     fp32_ops = {"ht_laplace": 3.5, "ht_fourier": 9.5, "ht_bessel": 7.5}
     ect_instr = 16.0
     if names[dom] == "extract":

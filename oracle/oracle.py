@@ -9,7 +9,7 @@ Source: Lebovici, Oudot, Passe, "Efficient computation of topological integral
 transforms" (SEA 2024, arXiv 2405.02256).  Every function cites the passage it
 follows (section, lemma, equation or table of the paper).
 
-Conventions (each one a reading of the paper, listed in the design doc):
+Conventions (each one a reading of the paper where it is silent or ambiguous):
 
 * An image with n axes is a numpy array in C order; the paper's coordinate 0 is the
   FASTEST memory axis (numpy's last axis).  Appendix A's cell keys show that the
