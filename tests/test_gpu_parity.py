@@ -44,6 +44,8 @@ def _images():
         "bern9x10x11": synth.bernoulli((9, 10, 11), 0.5, seed=6),
         "grf20x33x64": synth.grf((20, 33, 64), 4.0, seed=7),
         "cube2": np.full((2, 2, 2), 1, dtype=np.uint8),
+        "wide3d_3x4x1100": synth.uniform_u8((3, 4, 1100), seed=17),     # row pieces, unaligned rows
+        "wide3d_2x3x2048": synth.grf((2, 3, 2048), 3.0, seed=18),      # row pieces, aligned rows
         "grf40x40x48bin": synth.grf((40, 40, 48), 5.0, seed=8, binary=True),
         "i32_2d": rng.integers(-1000, 1000, size=(50, 70)).astype(np.int32),
         "i32_3d": rng.integers(-50, 50, size=(12, 13, 14)).astype(np.int32),
