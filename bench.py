@@ -464,6 +464,15 @@ def extra_workloads(dev):
     pipe.pixels.copy_(batch.pixels)
     pipe.capture()
     ms = _time_cuda(lambda: pipe.run(), reps=5)
+    # the three parts of the step, each launched on its own (outside the graph)
+    ect_d = torch.from_numpy(ect_h).to(dev)
+    ht_d = torch.from_numpy(ht_h).to(dev)
+    ect_o = torch.empty((len(imgs), 64, 64), dtype=torch.int32, device=dev)
+    ht_o = torch.empty((len(imgs), 256), dtype=torch.float64, device=dev)
+    ms_parts = {"extract_ms": _time_cuda(lambda: pipe.tables.build(pipe.pixels)),
+                "ect_ms": _time_cuda(lambda: tb.ect(pipe.tables, ect_d, -R2, R2, 64, out=ect_o)),
+                "laplace_ms": _time_cuda(lambda: tb.hybrid_transform(pipe.tables, "laplace", ht_d, "fp32c",
+                                                                     out=ht_o))}
     pipe.tables.sync()
     nl, nd = _sizes(pipe.tables, len(imgs), 4)
     terms = int((nd * np.bincount(_orthants(ht_h), minlength=4)[None, :]).sum())
@@ -473,7 +482,7 @@ def extra_workloads(dev):
                     "Laplace at 256 unit dirs per image; extraction + ECT + Laplace replayed as one CUDA graph",
         "ms_per_step": ms, "images_per_s": len(imgs) / (ms / 1e3), "pixels": px,
         "ect_dirs_per_s": len(imgs) * 64 / (ms / 1e3), "laplace_terms_per_s_whole_step": terms / (ms / 1e3),
-        "input_gen_s": gen_s}
+        "parts": ms_parts, "input_gen_s": gen_s}
     pipe.tables.free()
     del pipe, batch, imgs
 
