@@ -389,10 +389,10 @@ def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_
         adj[k] = {"ms": ms, "terms_per_s": terms / (ms / 1e3)}
     rows["adjoint_2d"] = {"workload": "same tables; 4096 dirs, d/dxi of sum_b,d HT", **adj}
 
-    # f3: kappa = sin (the kernel of the paper's experiments), on the Fourier path
+    # f3: kappa = sin (the kernel of the paper's experiments)
     o_sine = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
     ms = _time_cuda(lambda: tb.hybrid_transform(tabs, "sine", dirs_ht, "fp32c", out=o_sine), reps=1)
-    rows["sine_2d"] = {"workload": "same tables; 4096 dirs, kappa = sin (kbar = -cos) via the Fourier path",
+    rows["sine_2d"] = {"workload": "same tables; 4096 dirs, kappa = sin (kbar = -cos), FP32C",
                        "ms": ms, "terms_per_s": terms / (ms / 1e3)}
     del o_sine
 

@@ -73,10 +73,7 @@ typedef enum { TOPOT_VERTEX = 0, TOPOT_TOP = 1 } topot_construction;
  *   FOURIER  kbar(s) = sin s + i cos s (kappa(t) = e^{-i t}); output (re, im)
  *   BESSEL   kbar(s) = J_0(s)          (kappa = -J_1)
  *   SINE     kbar(s) = -cos s          (kappa = sin, the kernel of the experiments of
- *                                       Section 5); real output.  It runs on the
- *                                       Fourier path (HT_sine = -Im HT_Fourier) with a
- *                                       temporary (re, im) result in the handle, so
- *                                       hybrid_transform_noalloc does not take it.    */
+ *                                       Section 5); real output                      */
 typedef enum { TOPOT_LAPLACE = 0, TOPOT_FOURIER = 1, TOPOT_BESSEL = 2, TOPOT_SINE = 3 } topot_kernel;
 
 /* FP32C: FP32 terms, Kahan-compensated per thread, FP64 cross-block combine

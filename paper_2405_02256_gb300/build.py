@@ -58,7 +58,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     if force or not _newer(LIB, objs):
-        cmd = [cc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-cudart", "static"]
+        # every symbol resolved at link time: a missing kernel launcher fails the build
+        cmd = [cc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-cudart", "static", "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -18,10 +18,8 @@ int extract_block(int n);
 int extract_k(int n);
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
 cudaError_t launch_extract_u8(int n, const ExtractArgs& a, cudaStream_t st);
-cudaError_t launch_sine_from_fourier(const double* f, double* out, long long n, cudaStream_t st);
 cudaError_t launch_selftest_wait(int which, unsigned long long limit_ns, unsigned long long* flag, unsigned* err,
                                  cudaStream_t st);
-cudaError_t launch_sine_gout(const double* g, double* g2, long long n, cudaStream_t st);
 int extract_u8_threads(int n);
 int extract_u8_strip(int n);
 size_t extract_u8_smem_bytes(int n, int stage_bytes);
@@ -70,9 +68,6 @@ struct topot_tables {
     // host copies (valid after tables_sync)
     bool host_valid = false;
     std::vector<long long> h_seg_count, h_chi, h_absum;
-    // temporary (re, im) results of the sine kernel, grown on demand
-    void* aux = nullptr;
-    size_t aux_bytes = 0;
     // evaluation workspace, grown on demand
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -469,7 +464,6 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
 void free_tables(topot_tables* t) {
     if (!t) return;
     if (t->ws) cudaFree(t->ws);
-    if (t->aux) cudaFree(t->aux);
     if (t->top_buf) cudaFree(t->top_buf);
     if (t->arena_val) cudaFree(t->arena_val);
     if (t->arena_idx) cudaFree(t->arena_idx);
@@ -559,7 +553,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     topot_tables* t = const_cast<topot_tables*>(tc);
     if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out || (adjoint && !d_gout))
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
-    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL)
+    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL && kernel != TOPOT_SINE)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad kernel");
     if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
@@ -629,55 +623,16 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     return TOPOT_OK;
 }
 
-// The sine kernel's temporary [B][D][2] buffer in the handle (grown on demand).
-static topot_status ensure_aux(topot_tables* t, size_t bytes) {
-    if (t->aux_bytes >= bytes) return TOPOT_OK;
-    if (t->aux) {
-        cudaError_t e = cudaFree(t->aux);
-        t->aux = nullptr;
-        t->aux_bytes = 0;
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(sine buffer)");
-    }
-    cudaError_t e = cudaMalloc(&t->aux, bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(sine buffer)");
-    t->aux_bytes = bytes;
-    return TOPOT_OK;
-}
-
-topot_status hybrid_transform(const topot_tables* tc, topot_kernel kernel, topot_precision precision,
+topot_status hybrid_transform(const topot_tables* t, topot_kernel kernel, topot_precision precision,
                               const double* d_dirs, int D, int per_image_dirs, double* d_out, void* stream) {
-    if (kernel != TOPOT_SINE)
-        return ht_common("hybrid_transform", tc, kernel, precision, d_dirs, D, per_image_dirs, false, nullptr,
-                         d_out, stream);
-    topot_tables* t = const_cast<topot_tables*>(tc);
-    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out)
-        return fail(TOPOT_ERR_INVALID_ARG, "hybrid_transform: bad handle, directions or output");
-    const long long n = (long long)t->B * D;
-    topot_status s = ensure_aux(t, sizeof(double) * 2 * (size_t)n);
-    if (s != TOPOT_OK) return s;
-    double* f = reinterpret_cast<double*>(t->aux);
-    s = ht_common("hybrid_transform", t, TOPOT_FOURIER, precision, d_dirs, D, per_image_dirs, false, nullptr, f,
-                  stream);
-    if (s != TOPOT_OK) return s;
-    TOPOT_CUDA(launch_sine_from_fourier(f, d_out, n, reinterpret_cast<cudaStream_t>(stream)));
-    return TOPOT_OK;
+    return ht_common("hybrid_transform", t, kernel, precision, d_dirs, D, per_image_dirs, false, nullptr, d_out,
+                     stream);
 }
 
-topot_status hybrid_transform_grad(const topot_tables* tc, topot_kernel kernel, topot_precision precision,
+topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel, topot_precision precision,
                                    const double* d_dirs, int D, int per_image_dirs, const double* d_gout,
                                    double* d_gdirs, void* stream) {
-    if (kernel != TOPOT_SINE)
-        return ht_common("hybrid_transform_grad", tc, kernel, precision, d_dirs, D, per_image_dirs, true, d_gout,
-                         d_gdirs, stream);
-    topot_tables* t = const_cast<topot_tables*>(tc);
-    if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_gout || !d_gdirs)
-        return fail(TOPOT_ERR_INVALID_ARG, "hybrid_transform_grad: bad handle, directions or output");
-    const long long n = (long long)t->B * D;
-    topot_status s = ensure_aux(t, sizeof(double) * 2 * (size_t)n);
-    if (s != TOPOT_OK) return s;
-    double* g2 = reinterpret_cast<double*>(t->aux);
-    TOPOT_CUDA(launch_sine_gout(d_gout, g2, n, reinterpret_cast<cudaStream_t>(stream)));
-    return ht_common("hybrid_transform_grad", t, TOPOT_FOURIER, precision, d_dirs, D, per_image_dirs, true, g2,
+    return ht_common("hybrid_transform_grad", t, kernel, precision, d_dirs, D, per_image_dirs, true, d_gout,
                      d_gdirs, stream);
 }
 
@@ -735,7 +690,7 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
     const char* name = "hybrid_transform_noalloc";
     if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
-    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL)
+    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL && kernel != TOPOT_SINE)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad kernel");
     if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");

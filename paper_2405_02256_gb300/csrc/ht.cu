@@ -293,6 +293,13 @@ __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_
             k[0] = mul2(z, PATH == 2 ? sinc_short2(w) : sinc_long2(w));
             k[1] = PATH == 2 ? cos_short2(w) : cos_long2(w);
         }
+    } else if (KERNEL == TOPOT_SINE) {   // cos s; the sign of kbar = -cos is applied at the combine
+        if (mufu_cos) {
+            k[0] = make_float2(__cosf(z.x), __cosf(z.y));
+        } else {
+            const float2 w = mul2(z, z);
+            k[0] = PATH == 2 ? cos_short2(w) : cos_long2(w);
+        }
     } else {
         const float2 y = mul2(z, z);   // z is already halved
         k[0] = PATH == 2 ? j0_short2(y) : j0_long2(y);
@@ -308,7 +315,7 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
                                                 float2 (&s2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1],
                                                 float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
-    constexpr int BLK = KERNEL == TOPOT_FOURIER ? 4 : 8;
+    constexpr int BLK = (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE) ? 4 : 8;
     // [ws, we) is a multiple of BLK long (rounds are padded with zero-value points); each
     // block is summed in two interleaved chains (even / odd points) to halve the
     // dependency depth, then added with compensation.
@@ -378,12 +385,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
         // 0: scalar generic path; packed paths by the range of |<xi, v>| <= mloc:
-        //   Fourier: 2 (<= 0.75, short cos), 1 (<= 1.75, long cos)
+        //   Fourier, sine: 2 (<= 0.75, short cos), 1 (<= 1.75, long cos)
         //   Bessel:  2 (<= 1, short J0), 1 (<= 2, long J0)
         int path = 0;
         if (NPR > 0) {
             if (KERNEL == TOPOT_LAPLACE) path = 1;
-            else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
+            else if (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE)
+                path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
             else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
         }
 
@@ -415,6 +423,10 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
                             sincos_f(z, sn, cs);
                             kahan_add(acc[j][0], cmp[j][0], q.w * sn);
                             kahan_add(acc[j][1], cmp[j][1], q.w * cs);
+                        } else if (KERNEL == TOPOT_SINE) {
+                            float sn, cs;
+                            sincos_f(z, sn, cs);
+                            kahan_add(acc[j][0], cmp[j][0], q.w * cs);
                         } else {
                             kahan_add(acc[j][0], cmp[j][0], q.w * bessel_j0_f(z));
                         }
@@ -542,6 +554,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f64(EvalPlan P, TablesDev t, do
                     sincos(s, &sn, &cs);
                     acc[0] += q.w * sn;
                     acc[1] += q.w * cs;
+                } else if (KERNEL == TOPOT_SINE) {
+                    acc[0] += q.w * cos(s);
                 } else {
                     acc[0] += q.w * j0(s);
                 }
@@ -608,6 +622,15 @@ __device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int
                     }
                     t[0] = mul2(v2, cs);
                     t[1] = mul2(v2, sn);
+                } else if (KERNEL == TOPOT_SINE) {   // kappa = sin
+                    float2 sn;
+                    if (u & 1) {
+                        sn = make_float2(__sinf(z.x), __sinf(z.y));
+                    } else {
+                        const float2 ww = mul2(z, z);
+                        sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
+                    }
+                    t[0] = mul2(v2, sn);
                 } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
                     const float2 y = mul2(z, z);
                     const float2 j1 = mul2(z, PATH == 2 ? j1q_short2(y) : j1q_long2(y));
@@ -671,7 +694,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
         int path = 0;   // packed paths: as the forward, DL / 2 direction pairs per lane
         if (DL >= 2) {
             if (KERNEL == TOPOT_LAPLACE) path = 1;
-            else if (KERNEL == TOPOT_FOURIER) path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
+            else if (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE)
+                path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
             else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
         }
         if constexpr (DL >= 2) {
@@ -747,7 +771,15 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                             kahan_add(acc[j][NDIM + k], cmp[j][NDIM + k], ts * xs[k]);
                         }
                     } else {
-                        const float kv = KERNEL == TOPOT_LAPLACE ? exp2f(z) : -bessel_j1_f(z);
+                        float kv;
+                        if (KERNEL == TOPOT_LAPLACE) {
+                            kv = exp2f(z);
+                        } else if (KERNEL == TOPOT_SINE) {   // kappa = sin
+                            float cs;
+                            sincos_f(z, kv, cs);
+                        } else {
+                            kv = -bessel_j1_f(z);
+                        }
                         const float tk = q.w * kv;
 #pragma unroll
                         for (int k = 0; k < NDIM; ++k) kahan_add(acc[j][k], cmp[j][k], tk * xs[k]);
@@ -835,7 +867,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f64(EvalPlan P, TablesDev t
                         acc[NDIM + k] += q.w * sn * xs[k];
                     }
                 } else {
-                    const double kv = KERNEL == TOPOT_LAPLACE ? exp(s) : -j1(s);
+                    const double kv = KERNEL == TOPOT_LAPLACE ? exp(s) : (KERNEL == TOPOT_SINE ? sin(s) : -j1(s));
 #pragma unroll
                     for (int k = 0; k < NDIM; ++k) acc[k] += q.w * kv * xs[k];
                 }
@@ -886,7 +918,7 @@ __global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision
     double v[2];
     gather_partials(P, NO, tdh, nc, b, d, o, part, v);
     const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
-    double scale = sign;
+    double scale = kernel == TOPOT_SINE ? -sign : sign;   // sine: the partials hold sum v cos s
     if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
         double M = 0.0;
         for (int k = 0; k < n; ++k) M += fabs(xi[k]);
@@ -973,6 +1005,7 @@ static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel
         case TOPOT_LAPLACE: return launch_ht_k<NDIM, TOPOT_LAPLACE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         case TOPOT_FOURIER: return launch_ht_k<NDIM, TOPOT_FOURIER, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         case TOPOT_BESSEL: return launch_ht_k<NDIM, TOPOT_BESSEL, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        case TOPOT_SINE: return launch_ht_k<NDIM, TOPOT_SINE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -999,32 +1032,6 @@ cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, i
     const long long rows = (long long)P.nsets * P.D;
     k_ht_adj_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part,
                                                                        gout, gdirs);
-    return cudaGetLastError();
-}
-
-// kappa = sin on the Fourier path: HT_sine = -Im HT_Fourier, and its adjoint is the
-// Fourier adjoint with output weights (0, -g).
-__global__ void k_sine_from_fourier(const double* __restrict__ f, double* __restrict__ out, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = -f[2 * i + 1];
-}
-
-__global__ void k_sine_gout(const double* __restrict__ g, double* __restrict__ g2, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        g2[2 * i] = 0.0;
-        g2[2 * i + 1] = -g[i];
-    }
-}
-
-cudaError_t launch_sine_from_fourier(const double* f, double* out, long long n, cudaStream_t st) {
-    const unsigned grid = (unsigned)std::max(1ll, std::min((n + 255) / 256, 4096ll));
-    k_sine_from_fourier<<<grid, 256, 0, st>>>(f, out, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sine_gout(const double* g, double* g2, long long n, cudaStream_t st) {
-    const unsigned grid = (unsigned)std::max(1ll, std::min((n + 255) / 256, 4096ll));
-    k_sine_gout<<<grid, 256, 0, st>>>(g, g2, n);
     return cudaGetLastError();
 }
 

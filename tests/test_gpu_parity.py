@@ -197,7 +197,7 @@ def test_hybrid_transform_tiles(tb, dl):
     tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=2048)
     dirs = synth.random_2d_dirs(1100, 51, 0.01, 1.0)
     d = torch.from_numpy(dirs).cuda()
-    for kernel in ("laplace", "fourier", "bessel") if dl < 8 else ("laplace",):
+    for kernel in ("laplace", "fourier", "bessel", "sine") if dl < 8 else ("laplace",):
         got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
         want, norm = O.hybrid_transform(ref, kernel, dirs)
         assert _ht_err(got, want, norm, kernel) <= 1e-6
@@ -261,7 +261,7 @@ def test_gradient_tiles(tb, dl):
     dirs = synth.random_2d_dirs(600, 69, 0.05, 1.0)
     rng = np.random.default_rng(70)
     d = torch.from_numpy(dirs).cuda()
-    for kernel in ("laplace", "fourier", "bessel"):
+    for kernel in ("laplace", "fourier", "bessel", "sine"):
         nc = 2 if kernel == "fourier" else 1
         gout = rng.standard_normal((1, 600, 2)) if nc == 2 else rng.standard_normal((1, 600))
         got = tb.hybrid_transform_grad(tabs, kernel, d, torch.from_numpy(gout).cuda()).cpu().numpy()
