@@ -261,6 +261,90 @@ __device__ __forceinline__ FastDiv ldg_fastdiv(const FastDiv* f) {
 
 }  // namespace
 
+// Geometry of one tile (image b, local tile index lt).
+struct TileGeo {
+    int m0, m1, m2, W, R, spr, RS, segs, tpp, lt, z, y0, x0, rows, cols, packed;
+    long long tile_begin;
+    const uint8_t* img;
+};
+
+template <int NDIM>
+__device__ __forceinline__ TileGeo tile_geometry(const ExtractArgs& p, int b, long long ticket) {
+    const ImgDesc* Ip = p.t.img + b;
+    TileGeo g;
+    g.m0 = __ldg(&Ip->m[0]);
+    g.m1 = __ldg(&Ip->m[1]);
+    g.m2 = __ldg(&Ip->m[2]);
+    g.W = __ldg(&Ip->W);
+    g.R = __ldg(&Ip->R);
+    g.spr = __ldg(&Ip->spr);
+    g.RS = __ldg(&Ip->rs);
+    g.segs = __ldg(&Ip->segs_per_row);
+    g.tpp = __ldg(&Ip->tiles_per_plane);
+    g.packed = __ldg(&Ip->packed);
+    g.tile_begin = __ldg(&Ip->tile_begin);
+    g.lt = (int)(ticket - g.tile_begin);
+    g.z = NDIM == 3 ? (int)fastdiv((uint32_t)g.lt, ldg_fastdiv(&Ip->div_tpp)) : 0;
+    const int rem = g.lt - g.z * g.tpp;
+    const int rb = (int)fastdiv((uint32_t)rem, ldg_fastdiv(&Ip->div_segs));
+    const int sg = rem - rb * g.segs;
+    g.y0 = rb * g.R;
+    g.x0 = sg * g.W;
+    g.rows = min(g.R, g.m1 - g.y0);
+    g.cols = min(g.W, g.m0 - g.x0);
+    g.img = reinterpret_cast<const uint8_t*>(p.pixels) + __ldg(&Ip->offset);
+    return g;
+}
+
+// Bulk copies of the tile's staged rows, issued by one thread (the mbarrier counts the
+// bytes); rows that need plain loads or zeros are left to the block.
+template <int NDIM>
+__device__ __forceinline__ void issue_stage_copies(const TileGeo& g, uint8_t* stage, uint64_t* bar) {
+    constexpr int kNP = NDIM == 3 ? 3 : 1;
+    const int srows = g.rows + 2;
+    const int PS = (g.R + 2) * g.RS;
+    if (g.packed) {
+        if ((reinterpret_cast<uintptr_t>(g.img) & 15) != 0) {   // unaligned pixel buffer: plain loads
+            mbar_arrive_expect_tx(bar, 0u);
+            return;
+        }
+        unsigned bytes = 0;
+        for (int pl = 0; pl < kNP; ++pl) {
+            const int zz = g.z + pl - (NDIM == 3 ? 1 : 0);
+            if (zz < 0 || zz >= g.m2) continue;
+            bytes += (unsigned)((min(g.y0 + g.rows + 1, g.m1) - max(g.y0 - 1, 0)) * g.m0);
+        }
+        mbar_arrive_expect_tx(bar, bytes);
+        for (int pl = 0; pl < kNP; ++pl) {
+            const int zz = g.z + pl - (NDIM == 3 ? 1 : 0);
+            if (zz < 0 || zz >= g.m2) continue;
+            const int ylo = max(g.y0 - 1, 0), yhi = min(g.y0 + g.rows + 1, g.m1);
+            bulk_g2s(stage + kPadB + pl * PS + (ylo - (g.y0 - 1)) * g.m0,
+                     g.img + ((long long)zz * g.m1 + ylo) * g.m0, (unsigned)((yhi - ylo) * g.m0), bar);
+        }
+        return;
+    }
+    unsigned bytes = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            mbar_arrive_expect_tx(bar, bytes);
+            if (bytes == 0) return;
+        }
+        if ((g.cols & 15) != 0) continue;
+        for (int q = 0; q < kNP * srows; ++q) {
+            const int pl = NDIM == 3 ? q / srows : 0;
+            const int rr = q - pl * srows;
+            const int zz = g.z + pl - (NDIM == 3 ? 1 : 0);
+            const int yy = g.y0 + rr - 1;
+            if (zz < 0 || zz >= g.m2 || yy < 0 || yy >= g.m1) continue;
+            const uint8_t* src = g.img + ((long long)zz * g.m1 + yy) * g.m0 + g.x0;
+            if ((reinterpret_cast<uintptr_t>(src) & 15) != 0) continue;
+            if (pass == 0) bytes += (unsigned)g.cols;
+            else bulk_g2s(stage + pl * PS + rr * g.RS + kPadB, src, (unsigned)g.cols, bar);
+        }
+    }
+}
+
 template <int NDIM>
 __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u8(ExtractArgs p) {
     using Ly = U8Layout<NDIM>;
@@ -275,7 +359,6 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     uint32_t* sh_wex = reinterpret_cast<uint32_t*>(smem_raw + Ly::OFF_WEX);
     uint32_t* sh_tot = reinterpret_cast<uint32_t*>(smem_raw + Ly::OFF_TOT);
     long long* sh_pref = reinterpret_cast<long long*>(smem_raw + Ly::OFF_PREF);
-    int* sh_red = reinterpret_cast<int*>(smem_raw + Ly::OFF_RED);
     uint32_t* out = reinterpret_cast<uint32_t*>(smem_raw + Ly::OFF_OUT);
     uint8_t* stage = smem_raw + Ly::OFF_STAGE;
 
@@ -295,28 +378,20 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
         }
         sh_int[0] = (int)ticket;
         sh_int[1] = lo;
+        // the tile's bulk copies go out before the block synchronises
+        issue_stage_copies<NDIM>(tile_geometry<NDIM>(p, lo, ticket), stage, bar);
     }
-    if (tid < 1 + kNO) sh_red[tid] = 0;
     __syncthreads();
 
     const long long ticket = (unsigned)sh_int[0];
     const int b = sh_int[1];
     const ImgDesc* Ip = T.img + b;
-    const int m0 = __ldg(&Ip->m[0]), m1 = __ldg(&Ip->m[1]), m2 = __ldg(&Ip->m[2]);
-    const int W = __ldg(&Ip->W), R = __ldg(&Ip->R);
-    const int spr = __ldg(&Ip->spr), RS = __ldg(&Ip->rs);
-    const int segs = __ldg(&Ip->segs_per_row), tpp = __ldg(&Ip->tiles_per_plane);
-    const long long tile_begin = __ldg(&Ip->tile_begin);
-    const int lt = (int)(ticket - tile_begin);
-    const int z = NDIM == 3 ? (int)fastdiv((uint32_t)lt, ldg_fastdiv(&Ip->div_tpp)) : 0;
-    const int rem = lt - z * tpp;
-    const int rb = (int)fastdiv((uint32_t)rem, ldg_fastdiv(&Ip->div_segs));
-    const int sg = rem - rb * segs;
-    const int y0 = rb * R, x0 = sg * W;
-    const int rows = min(R, m1 - y0);
-    const int cols = min(W, m0 - x0);
+    const TileGeo G = tile_geometry<NDIM>(p, b, ticket);
+    const int m0 = G.m0, m1 = G.m1, m2 = G.m2, R = G.R, spr = G.spr, RS = G.RS, tpp = G.tpp;
+    const long long tile_begin = G.tile_begin;
+    const int lt = G.lt, z = G.z, y0 = G.y0, x0 = G.x0, rows = G.rows, cols = G.cols;
     const int L0 = (z * m1 + y0) * m0 + x0;            // linear index of the tile's first vertex
-    const uint8_t* img = reinterpret_cast<const uint8_t*>(p.pixels) + __ldg(&Ip->offset);
+    const uint8_t* img = G.img;
 
     // ---- 1. stage rows y0 - 1 .. y0 + rows (planes z - 1 .. z + 1); zeros outside ----------
     // Packed images (full-row tiles, m_0 and the image offset multiples of 16): the rows of
@@ -330,7 +405,6 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     if (packed) {
         // bulk copies need a 16-byte aligned source: the pixel buffer itself may not be
         const bool bulk = (reinterpret_cast<uintptr_t>(img) & 15) == 0;
-        if (tid == 0 && !bulk) mbar_arrive_expect_tx(bar, 0u);
         if (!bulk) {
             for (int pl = 0; pl < kNP; ++pl) {
                 const int zz = z + pl - (NDIM == 3 ? 1 : 0);
@@ -339,22 +413,6 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
                 uint8_t* dst = stage + kPadB + pl * PS + (ylo - (y0 - 1)) * m0;
                 const uint8_t* src = img + ((long long)zz * m1 + ylo) * m0;
                 for (int c = tid; c < (yhi - ylo) * m0; c += kB) dst[c] = src[c];
-            }
-        }
-        if (tid == 0 && bulk) {
-            unsigned bytes = 0;
-            for (int pl = 0; pl < kNP; ++pl) {
-                const int zz = z + pl - (NDIM == 3 ? 1 : 0);
-                if (zz < 0 || zz >= m2) continue;
-                bytes += (unsigned)((min(y0 + rows + 1, m1) - max(y0 - 1, 0)) * m0);
-            }
-            mbar_arrive_expect_tx(bar, bytes);
-            for (int pl = 0; pl < kNP; ++pl) {
-                const int zz = z + pl - (NDIM == 3 ? 1 : 0);
-                if (zz < 0 || zz >= m2) continue;
-                const int ylo = max(y0 - 1, 0), yhi = min(y0 + rows + 1, m1);
-                bulk_g2s(stage + kPadB + pl * PS + (ylo - (y0 - 1)) * m0, img + ((long long)zz * m1 + ylo) * m0,
-                         (unsigned)((yhi - ylo) * m0), bar);
             }
         }
         // rows and planes outside the image: zeros (16-byte stores; m_0 is a multiple of 16)
@@ -382,25 +440,6 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
             const int pl = NDIM == 3 ? q / srows : 0;
             return stage + pl * PS + (q - pl * srows) * RS + kPadB;
         };
-        if (tid == 0) {
-            unsigned bytes = 0;
-            if ((cols & 15) == 0) {
-                for (int q = 0; q < kNP * srows; ++q) {
-                    bool inside;
-                    const uint8_t* src = src_row(q, inside);
-                    if (inside && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) bytes += (unsigned)cols;
-                }
-            }
-            mbar_arrive_expect_tx(bar, bytes);
-            if (bytes) {
-                for (int q = 0; q < kNP * srows; ++q) {
-                    bool inside;
-                    const uint8_t* src = src_row(q, inside);
-                    if (inside && ((reinterpret_cast<uintptr_t>(src) & 15) == 0))
-                        bulk_g2s(dst_row(q), src, (unsigned)cols, bar);
-                }
-            }
-        }
         for (int q = warp; q < kNP * srows; q += kNW) {
             uint8_t* dst = dst_row(q);
             bool inside;
@@ -642,16 +681,16 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
             cum += (uint32_t)ngroups;
         }
     }
+    // per-warp sums straight to the image totals (no block barrier at the end)
 #pragma unroll
     for (int i = 0; i <= kNO; ++i) {
         const int v = (int)__reduce_add_sync(kFull, (unsigned)red[i]);
-        if (lane == 0) atomicAdd(&sh_red[i], v);
+        if (lane == 0 && v != 0) {
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(i == 0 ? &T.chi[b]
+                                                                                 : &T.absum[(long long)b * kNO + i - 1]);
+            atomicAdd(dst, (unsigned long long)(long long)v);
+        }
     }
-    __syncthreads();
-    if (tid == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&T.chi[b]), (unsigned long long)(long long)sh_red[0]);
-    if (tid >= 1 && tid <= kNO)
-        atomicAdd(reinterpret_cast<unsigned long long*>(&T.absum[(long long)b * kNO + tid - 1]),
-                  (unsigned long long)(long long)sh_red[tid]);
 }
 
 // ---- host side ----------------------------------------------------------------------------
