@@ -43,7 +43,7 @@ __all__ = [
     "CriticalTables", "critical_tables", "euler_characteristic", "thresholds",
     "dot_products", "vertex_positions", "ect_exact", "ect_eval", "ect_values",
     "radon_values", "radon_exact", "radon_exact_eval", "ect_grid", "radon_grid",
-    "radon_grid_lemma", "KERNELS", "hybrid_transform", "hybrid_transform_grad",
+    "radon_grid_lemma", "KERNELS", "table_kernel", "hybrid_transform", "hybrid_transform_grad",
 ]
 
 
@@ -499,6 +499,48 @@ KERNELS = {
 }
 
 
+def table_kernel(values, s_min: float, s_max: float):
+    """A kernel given by samples of its primitive: (kbar, kappa) callables.
+
+    Section 2.2 admits any locally integrable kernel kappa; Lemma 3.1 needs only its
+    primitive kbar.  Here kbar is given by K >= 2 samples y_i = kbar(a + i h),
+    h = (b - a) / (K - 1), i = 0 .. K - 1 (a = s_min < b = s_max), and is read as the
+    piecewise-linear interpolant of the samples, constant outside [a, b]:
+        u = (s - a) / h;  i = floor(u), f = u - i         (0 <= u < K - 1)
+        kbar(s) = y_i + f (y_{i+1} - y_i);  y_0 for u < 0;  y_{K-1} for u >= K - 1.
+    Its derivative kappa is the step function (y_{i+1} - y_i) / h on [a + i h,
+    a + (i + 1) h) and zero outside [a, b) (the right derivative at the knots).
+    """
+    y = np.asarray(values, dtype=np.float64).ravel()
+    K = y.size
+    a, b = float(s_min), float(s_max)
+    if K < 2 or not (a < b) or not np.all(np.isfinite(y)):
+        raise ValueError("table kernel: need K >= 2 finite samples and s_min < s_max")
+    h = (b - a) / (K - 1)
+
+    def _seg(s):
+        u = (np.asarray(s, dtype=np.float64) - a) / h
+        inside = (u >= 0.0) & (u < K - 1)
+        i = np.where(inside, np.floor(np.where(inside, u, 0.0)), 0.0).astype(np.int64)
+        return u, inside, i
+
+    def kbar(s):
+        u, inside, i = _seg(s)
+        f = u - i
+        mid = y[i] + f * (y[i + 1] - y[i])
+        return np.where(inside, mid, np.where(u < 0.0, y[0], y[K - 1]))
+
+    def kappa(s):
+        u, inside, i = _seg(s)
+        return np.where(inside, (y[i + 1] - y[i]) / h, 0.0)
+
+    return kbar, kappa
+
+
+def _kernel_pair(kernel):
+    return KERNELS[kernel] if isinstance(kernel, str) else kernel
+
+
 def _ht_terms(tab: CriticalTables, xi):
     n = tab.n
     half = 1 << (n - 1)
@@ -520,13 +562,14 @@ def hybrid_transform(tab: CriticalTables, kernel: str, dirs):
 
     With Delta_eps = -Delta^ord_eps this is sum_v Delta_eps(v) kbar(<xi, v>); the
     sum is taken exactly (math.fsum) over the FP64 terms.  The primitive's constant
-    drops out because sum_v Delta_eps(v) = 0.  Returns (values, norms): values is
+    drops out because sum_v Delta_eps(v) = 0.  ``kernel`` is a name of KERNELS or a
+    real (kbar, kappa) pair such as table_kernel() returns.  Returns (values, norms): values is
     float64 [D] (complex128 for Fourier), norms[d] = sum_v |Delta kbar| (complex
     modulus for Fourier) -- the scale for relative errors.
     """
-    kbar, _ = KERNELS[kernel]
+    kbar, _ = _kernel_pair(kernel)
     dirs = np.asarray(dirs, dtype=np.float64).reshape(-1, tab.n)
-    cplx = kernel == "fourier"
+    cplx = isinstance(kernel, str) and kernel == "fourier"
     vals = np.zeros(dirs.shape[0], dtype=np.complex128 if cplx else np.float64)
     norms = np.zeros(dirs.shape[0], dtype=np.float64)
     for d, xi in enumerate(dirs):
@@ -544,10 +587,10 @@ def hybrid_transform_grad(tab: CriticalTables, kernel: str, dirs):
     move inside an orthant (Lemma 3.2).  Returns (grad, norms): grad is [D, n]
     (complex128 for Fourier: d Re / d xi + i d Im / d xi); norms[d, k] = sum |terms|.
     """
-    _, kap = KERNELS[kernel]
+    _, kap = _kernel_pair(kernel)
     dirs = np.asarray(dirs, dtype=np.float64).reshape(-1, tab.n)
     n = tab.n
-    cplx = kernel == "fourier"
+    cplx = isinstance(kernel, str) and kernel == "fourier"
     g = np.zeros((dirs.shape[0], n), dtype=np.complex128 if cplx else np.float64)
     norms = np.zeros((dirs.shape[0], n), dtype=np.float64)
     for d, xi in enumerate(dirs):

@@ -375,3 +375,105 @@ def test_orthant_rule():
     x = O.vertex_coords(7)
     np.testing.assert_array_equal(x, -x[::-1])
     assert x[0] == -0.5 and x[-1] == 0.5
+
+
+# ---------------------------------------------------------------- tabulated kernels
+
+def _table_dirs(rng, n, count):
+    return [d * 1.5 for d in _generic_dirs(n, rng, count=count)]
+
+
+def test_table_kernel_interpolant():
+    """Samples at the knots, linear in between, constant outside, kappa = slope."""
+    rng = np.random.default_rng(61)
+    y = rng.normal(size=9)
+    a, b = -0.7, 1.3
+    kbar, kap = O.table_kernel(y, a, b)
+    h = (b - a) / 8
+    knots = a + h * np.arange(9)
+    np.testing.assert_allclose(kbar(knots), y, rtol=0, atol=1e-14)
+    mids = knots[:-1] + 0.5 * h
+    np.testing.assert_allclose(kbar(mids), 0.5 * (y[:-1] + y[1:]), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(kap(mids), (y[1:] - y[:-1]) / h, rtol=1e-12)
+    np.testing.assert_array_equal(kbar(np.array([-5.0, a - 1e-9])), [y[0], y[0]])
+    np.testing.assert_array_equal(kbar(np.array([b, b + 1e-9, 7.0])), [y[-1]] * 3)
+    np.testing.assert_array_equal(kap(np.array([-5.0, b, 7.0])), [0.0, 0.0, 0.0])
+    # kappa is the derivative of kbar away from the knots
+    s = knots[:-1] + h * rng.uniform(0.1, 0.9, size=8)
+    e = 1e-7 * h
+    np.testing.assert_allclose((kbar(s + e) - kbar(s - e)) / (2 * e), kap(s), rtol=1e-6)
+    # samples of an affine function are reproduced everywhere on [a, b]
+    lin, _ = O.table_kernel(2.0 * knots - 3.0, a, b)
+    t = np.linspace(a, b, 101)
+    np.testing.assert_allclose(lin(t), 2.0 * t - 3.0, rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        O.table_kernel([1.0], a, b)
+    with pytest.raises(ValueError):
+        O.table_kernel(y, b, a)
+
+
+def test_table_ht_against_cells():
+    """Lemma 3.1 with a tabulated primitive against the cell-by-cell integral (any kbar)."""
+    rng = np.random.default_rng(62)
+    for img in _tiny_images()[::2]:
+        tab = O.critical_tables(img)
+        M = 0.5 * img.ndim
+        # a table that covers only part of the dot products: the constant ends count too
+        kt = O.table_kernel(rng.normal(size=7), -0.4 * M, 0.5 * M)
+        for xi in _table_dirs(rng, img.ndim, 1):
+            val, norm = O.hybrid_transform(tab, kt, [xi])
+            cellsum = B.integral_kappa_radon(img, xi, kt[0])
+            assert abs(val[0] + cellsum) <= 1e-12 * max(1.0, norm[0])
+
+
+def test_table_ht_outside_range_vanishes():
+    # kbar constant on every dot product: HT = c * sum_v Delta_eps(v) = 0
+    img = synth.grf((10, 12), 2.0, seed=63)
+    tab = O.critical_tables(img)
+    dirs = _table_dirs(np.random.default_rng(64), 2, 3)
+    for a, b in [(5.0, 6.0), (-9.0, -5.0)]:
+        val, _ = O.hybrid_transform(tab, O.table_kernel([2.5, -1.0, 4.0], a, b), dirs)
+        np.testing.assert_array_equal(val, 0.0)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_table_converges_to_laplace(n):
+    """Samples of e^s: |HT_table - HT_laplace| <= h^2 / 8 max e^s sum |Delta| (linear
+    interpolation error); the gradient within h max e^s sum |Delta x_k|."""
+    shape = (9, 11) if n == 2 else (5, 6, 7)
+    img = synth.grf(shape, 2.0, seed=65)
+    tab = O.critical_tables(img)
+    dirs = _table_dirs(np.random.default_rng(66), n, 2)
+    M = max(0.5 * float(np.sum(np.abs(d))) for d in dirs)
+    for K in (65, 257):
+        # strictly wider than the dot products: at s = b itself kappa is the constant
+        # extension's (zero), and the extreme corners reach |s| = M exactly
+        a, b = -1.01 * M, 1.01 * M
+        h = (b - a) / (K - 1)
+        kt = O.table_kernel(np.exp(a + h * np.arange(K)), a, b)
+        got, _ = O.hybrid_transform(tab, kt, dirs)
+        want, _ = O.hybrid_transform(tab, "laplace", dirs)
+        gt, _ = O.hybrid_transform_grad(tab, kt, dirs)
+        gw, _ = O.hybrid_transform_grad(tab, "laplace", dirs)
+        for di, xi in enumerate(dirs):
+            _, _, dv = O.oracle._ht_terms(tab, xi)
+            l1 = float(np.sum(np.abs(dv)))
+            assert abs(got[di] - want[di]) <= h * h / 8 * math.exp(b) * l1 + 1e-12
+            assert np.max(np.abs(gt[di] - gw[di])) <= h * math.exp(b) * l1 * 0.5 + 1e-12
+
+
+def test_table_gradient_central_differences():
+    img = synth.grf((9, 11), 2.0, seed=67)
+    tab = O.critical_tables(img)
+    rng = np.random.default_rng(68)
+    kt = O.table_kernel(np.cumsum(rng.normal(size=33)) * 0.1, -1.1, 1.2)
+    h = 1e-7
+    dirs = [d for d in _table_dirs(rng, 2, 3) if np.min(np.abs(d)) > 10 * h]
+    g, _ = O.hybrid_transform_grad(tab, kt, dirs)
+    for di, xi in enumerate(dirs):
+        for k in range(2):
+            e = np.zeros(2)
+            e[k] = h
+            fp, _ = O.hybrid_transform(tab, kt, [xi + e])
+            fm, _ = O.hybrid_transform(tab, kt, [xi - e])
+            assert abs((fp[0] - fm[0]) / (2 * h) - g[di, k]) < 1e-5 * max(1.0, abs(g[di, k]))
