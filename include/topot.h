@@ -73,8 +73,10 @@ typedef enum { TOPOT_VERTEX = 0, TOPOT_TOP = 1 } topot_construction;
  *   FOURIER  kbar(s) = sin s + i cos s (kappa(t) = e^{-i t}); output (re, im)
  *   BESSEL   kbar(s) = J_0(s)          (kappa = -J_1)
  *   SINE     kbar(s) = -cos s          (kappa = sin, the kernel of the experiments of
- *                                       Section 5); real output                      */
-typedef enum { TOPOT_LAPLACE = 0, TOPOT_FOURIER = 1, TOPOT_BESSEL = 2, TOPOT_SINE = 3 } topot_kernel;
+ *                                       Section 5); real output
+ *   TABLE    kbar given by samples (kernel_table_create); only through
+ *            hybrid_transform_table / hybrid_transform_table_grad               */
+typedef enum { TOPOT_LAPLACE = 0, TOPOT_FOURIER = 1, TOPOT_BESSEL = 2, TOPOT_SINE = 3, TOPOT_TABLE = 4 } topot_kernel;
 
 /* FP32C: FP32 terms, Kahan-compensated per thread, FP64 cross-block combine
  *        (Laplace evaluated as e^{M} e^{s - M}, M = sum_k |xi_k| / 2, so no term
@@ -259,6 +261,40 @@ TOPOT_API topot_status hybrid_transform_noalloc(const topot_tables* t, topot_ker
                                                topot_precision precision, const double* d_dirs,
                                                int D, int per_image_dirs, double* d_out,
                                                void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Tabulated kernels (Section 2.2 admits any locally integrable kappa; Lemma 3.1 needs
+ * only its primitive kbar)
+ * ---------------------------------------------------------------------------
+ * h_values[i] = kbar(s_min + i h), i < K, h = (s_max - s_min) / (K - 1) (FP64, host,
+ * copied; the caller keeps ownership).  kbar is the piecewise-linear interpolant of the
+ * samples, constant outside [s_min, s_max]:
+ *   u = (s - s_min) / h, i = floor(u), f = u - i:  kbar(s) = y_i + f (y_{i+1} - y_i)
+ *   for 0 <= u < K - 1;  y_0 for u < 0;  y_{K-1} for u >= K - 1,
+ * and kappa = kbar' the step function (y_{i+1} - y_i) / h on [s_min + i h,
+ * s_min + (i + 1) h), zero outside [s_min, s_max).  2 <= K <= 16384, finite samples,
+ * s_min < s_max (finite), else INVALID_ARG.  The handle owns device copies on the
+ * current device (for FP32C, K + 1 FP32 pairs: (y_0, 0), (y_r + d_r / 2, d_r) per
+ * segment r with d_r = y_{r+1} - y_r, (y_{K-1}, 0); for FP64 the samples); free it with
+ * kernel_table_free after the last call that uses it has completed. */
+typedef struct topot_ktable topot_ktable;
+TOPOT_API topot_status kernel_table_create(const double* h_values, int K, double s_min, double s_max,
+                                           topot_ktable** out);
+TOPOT_API void kernel_table_free(topot_ktable* k);
+
+/* hybrid_transform / hybrid_transform_grad with the tabulated kernel k (real output,
+ * d_out [B][D]; the gradient as hybrid_transform_grad).  FP32C accuracy:
+ * |HT - exact| <= 1e-6 sum_v |Delta kbar| when |kappa| (s_max - s_min) is of the order of
+ * |kbar| (the FP32 position u carries an absolute error of a few units of 2^-24 K).
+ * Gradient: at a dot product within rounding of a knot either neighbouring slope may be
+ * taken. */
+TOPOT_API topot_status hybrid_transform_table(const topot_tables* t, const topot_ktable* k,
+                                              topot_precision precision, const double* d_dirs, int D,
+                                              int per_image_dirs, double* d_out, void* stream);
+TOPOT_API topot_status hybrid_transform_table_grad(const topot_tables* t, const topot_ktable* k,
+                                                   topot_precision precision, const double* d_dirs, int D,
+                                                   int per_image_dirs, const double* d_gout, double* d_gdirs,
+                                                   void* stream);
 
 /* Self-test of the bounded device-side waits.  Every spin of the library (extraction
  * look-back, wait for staged pixels) gives up after a time limit, records the timeout

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libtopot.so")
 U8, I32 = 0, 1
 VERTEX, TOP = 0, 1
 KERNELS = {"laplace": 0, "fourier": 1, "bessel": 2, "sine": 3}
+TABLE = 4
 PRECISIONS = {"fp32c": 0, "fp64": 1}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "OVERFLOW", 6: "TIMEOUT"}
 
@@ -27,7 +28,8 @@ API_SYMBOLS = (
     "build_critical_tables", "tables_create", "tables_build", "tables_sync", "tables_info",
     "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
     "hybrid_transform_grad", "hybrid_transform_noalloc", "exact_representation", "ect_exact_eval",
-    "radon_exact_eval", "topot_selftest_wait", "topot_last_error",
+    "radon_exact_eval", "topot_selftest_wait", "topot_last_error", "kernel_table_create", "kernel_table_free",
+    "hybrid_transform_table", "hybrid_transform_table_grad",
 )
 
 
@@ -76,6 +78,9 @@ def load(path: str = LIB_PATH):
         "ect_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
         "radon_exact_eval": [i32, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, i32, vp, vp],
         "topot_selftest_wait": [i32, i32, vp],
+        "kernel_table_create": [vp, i32, dp, dp, pp],
+        "hybrid_transform_table": [vp, vp, i32, vp, i32, i32, vp, vp],
+        "hybrid_transform_table_grad": [vp, vp, i32, vp, i32, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -83,6 +88,8 @@ def load(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     L.free_tables.argtypes = [vp]
     L.free_tables.restype = None
+    L.kernel_table_free.argtypes = [vp]
+    L.kernel_table_free.restype = None
     L.topot_last_error.argtypes = []
     L.topot_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -340,20 +347,58 @@ def radon_exact_eval(rep_lower: ExactRep, rep_ord: ExactRep, t, stream=None) -> 
     return out
 
 
-def hybrid_transform(tables: Tables, kernel: str, dirs: torch.Tensor, precision: str = "fp32c", out=None,
+class KernelTable:
+    """A kernel given by K samples of its primitive, kbar(s_min + i h), h = (s_max - s_min) / (K - 1):
+    piecewise-linear in between, constant outside (include/topot.h, kernel_table_create).
+    Pass it as the ``kernel`` of hybrid_transform / hybrid_transform_grad / HybridTransform."""
+
+    def __init__(self, values, s_min: float, s_max: float):
+        L = load()
+        y = np.ascontiguousarray(np.asarray(values, dtype=np.float64).ravel())
+        h = ctypes.c_void_p()
+        _check(L.kernel_table_create(y.ctypes.data_as(ctypes.c_void_p), int(y.size), float(s_min), float(s_max),
+                                     ctypes.byref(h)))
+        self._h = h
+        self.K, self.s_min, self.s_max = int(y.size), float(s_min), float(s_max)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("kernel table already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            torch.cuda.synchronize()
+            load().kernel_table_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hybrid_transform(tables: Tables, kernel, dirs: torch.Tensor, precision: str = "fp32c", out=None,
                      stream=None):
-    """HT(xi_d) per image: float64 [B, D] (Fourier: [B, D, 2] = (re, im))."""
+    """HT(xi_d) per image: float64 [B, D] (Fourier: [B, D, 2] = (re, im)).  ``kernel`` is a
+    name of KERNELS or a KernelTable."""
     L = load()
     dirs, D, per = _dirs(dirs, tables.n, tables.B)
     shape = (tables.B, D, 2) if kernel == "fourier" else (tables.B, D)
     if out is None:
         out = torch.empty(shape, dtype=torch.float64, device=dirs.device)
+    if isinstance(kernel, KernelTable):
+        _check(L.hybrid_transform_table(tables.handle, kernel.handle, PRECISIONS[precision], _ptr(dirs), D, per,
+                                        _ptr(out), _stream(stream)))
+        return out
     _check(L.hybrid_transform(tables.handle, KERNELS[kernel], PRECISIONS[precision], _ptr(dirs), D, per,
                               _ptr(out), _stream(stream)))
     return out
 
 
-def hybrid_transform_grad(tables: Tables, kernel: str, dirs: torch.Tensor, gout: torch.Tensor,
+def hybrid_transform_grad(tables: Tables, kernel, dirs: torch.Tensor, gout: torch.Tensor,
                           precision: str = "fp32c", out=None, stream=None):
     """sum over outputs of gout * dHT/dxi, shaped like dirs (float64)."""
     L = load()
@@ -361,6 +406,10 @@ def hybrid_transform_grad(tables: Tables, kernel: str, dirs: torch.Tensor, gout:
     gout = gout.contiguous().to(torch.float64)
     if out is None:
         out = torch.empty_like(dirs)
+    if isinstance(kernel, KernelTable):
+        _check(L.hybrid_transform_table_grad(tables.handle, kernel.handle, PRECISIONS[precision], _ptr(dirs), D,
+                                             per, _ptr(gout), _ptr(out), _stream(stream)))
+        return out
     _check(L.hybrid_transform_grad(tables.handle, KERNELS[kernel], PRECISIONS[precision], _ptr(dirs), D, per,
                                    _ptr(gout), _ptr(out), _stream(stream)))
     return out

@@ -38,6 +38,14 @@ cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, i
 
 using namespace topot;
 
+struct topot_ktable {
+    int K = 0;
+    double a = 0.0, h = 0.0;
+    int device = 0;
+    float2* d32 = nullptr;    // K + 1 padded pairs (see kernel_table_create)
+    double* d64 = nullptr;    // y_i
+};
+
 struct topot_tables {
     int n = 0, B = 0, NO = 0, S = 0;
     topot_dtype dtype = TOPOT_U8;
@@ -549,12 +557,18 @@ topot_status radon(const topot_tables* t, const double* d_dirs, int D, int per_i
 
 static topot_status ht_common(const char* name, const topot_tables* tc, topot_kernel kernel,
                               topot_precision precision, const double* d_dirs, int D, int per_image_dirs,
-                              bool adjoint, const double* d_gout, double* d_out, void* stream) {
+                              bool adjoint, const double* d_gout, double* d_out, void* stream,
+                              const topot_ktable* kt = nullptr) {
     topot_tables* t = const_cast<topot_tables*>(tc);
     if (!valid_dirs_args(t, d_dirs, D, per_image_dirs) || !d_out || (adjoint && !d_gout))
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad handle, directions or output");
-    if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL && kernel != TOPOT_SINE)
+    if (kernel == TOPOT_TABLE) {
+        if (!kt) return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": TABLE needs hybrid_transform_table");
+        if (kt->device != t->device)
+            return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": kernel table on another device");
+    } else if (kernel != TOPOT_LAPLACE && kernel != TOPOT_FOURIER && kernel != TOPOT_BESSEL && kernel != TOPOT_SINE) {
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad kernel");
+    }
     if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -570,7 +584,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
         }
         if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
         // adjoint: two direction pairs per lane for the one-component kernels in 2-D, else one
-        if (adjoint) dl = std::min(dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
+        if (adjoint && kernel != TOPOT_TABLE) dl = std::min(dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
     }
     const int tdh = 32 * dl;
     const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
@@ -610,6 +624,13 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     P.pair_chunks = cv.take<int>(npairs);
     P.thr = nullptr;
     P.T = 0;
+    if (kernel == TOPOT_TABLE) {
+        P.ktab = kt->d32;
+        P.ktab64 = kt->d64;
+        P.ktab_k = kt->K;
+        P.ktab_a = kt->a;
+        P.ktab_h = kt->h;
+    }
     double* part = cv.take<double>(part_elems);
 
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
@@ -634,6 +655,67 @@ topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel, t
                                    double* d_gdirs, void* stream) {
     return ht_common("hybrid_transform_grad", t, kernel, precision, d_dirs, D, per_image_dirs, true, d_gout,
                      d_gdirs, stream);
+}
+
+// ---- tabulated kernels ----------------------------------------------------------------------
+
+topot_status kernel_table_create(const double* h_values, int K, double s_min, double s_max, topot_ktable** out) {
+    if (!out) return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: out is NULL");
+    *out = nullptr;
+    if (!h_values || K < 2 || K > 16384)
+        return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: need 2 <= K <= 16384 samples");
+    if (!std::isfinite(s_min) || !std::isfinite(s_max) || !(s_min < s_max))
+        return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: need finite s_min < s_max");
+    for (int i = 0; i < K; ++i)
+        if (!std::isfinite(h_values[i])) return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: non-finite sample");
+    topot_ktable* k = new (std::nothrow) topot_ktable;
+    if (!k) return fail(TOPOT_ERR_OOM, "kernel_table_create: host allocation");
+    k->K = K;
+    k->a = s_min;
+    k->h = (s_max - s_min) / (double)(K - 1);
+    // FP32 layout of the evaluation kernels: K + 1 pairs, (y_0, 0), then per segment r
+    // (y_r + d_r / 2, d_r) with d_r = y_{r+1} - y_r, then (y_{K-1}, 0)
+    std::vector<float2> pairs((size_t)K + 1);
+    pairs[0] = make_float2((float)h_values[0], 0.0f);
+    for (int r = 0; r + 1 < K; ++r) {
+        const double d = h_values[r + 1] - h_values[r];
+        pairs[r + 1] = make_float2((float)(h_values[r] + 0.5 * d), (float)d);
+    }
+    pairs[K] = make_float2((float)h_values[K - 1], 0.0f);
+    cudaError_t e = cudaGetDevice(&k->device);
+    if (e == cudaSuccess) e = cudaMalloc(&k->d32, sizeof(float2) * ((size_t)K + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&k->d64, sizeof(double) * (size_t)K);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(k->d32, pairs.data(), sizeof(float2) * ((size_t)K + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(k->d64, h_values, sizeof(double) * (size_t)K, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        kernel_table_free(k);
+        return cuda_fail(e, "kernel_table_create");
+    }
+    *out = k;
+    return TOPOT_OK;
+}
+
+void kernel_table_free(topot_ktable* k) {
+    if (!k) return;
+    if (k->d32) cudaFree(k->d32);
+    if (k->d64) cudaFree(k->d64);
+    delete k;
+}
+
+topot_status hybrid_transform_table(const topot_tables* t, const topot_ktable* k, topot_precision precision,
+                                    const double* d_dirs, int D, int per_image_dirs, double* d_out, void* stream) {
+    if (!k) return fail(TOPOT_ERR_INVALID_ARG, "hybrid_transform_table: kernel table is NULL");
+    return ht_common("hybrid_transform_table", t, TOPOT_TABLE, precision, d_dirs, D, per_image_dirs, false, nullptr,
+                     d_out, stream, k);
+}
+
+topot_status hybrid_transform_table_grad(const topot_tables* t, const topot_ktable* k, topot_precision precision,
+                                         const double* d_dirs, int D, int per_image_dirs, const double* d_gout,
+                                         double* d_gdirs, void* stream) {
+    if (!k) return fail(TOPOT_ERR_INVALID_ARG, "hybrid_transform_table_grad: kernel table is NULL");
+    return ht_common("hybrid_transform_table_grad", t, TOPOT_TABLE, precision, d_dirs, D, per_image_dirs, true,
+                     d_gout, d_gdirs, stream, k);
 }
 
 }  // extern "C"

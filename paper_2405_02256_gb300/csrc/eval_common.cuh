@@ -34,6 +34,13 @@ struct EvalPlan {
     double* thr;               // [T] thresholds (ECT / Radon)
     int T;
     double t_min, t_max;
+    // tabulated kernel (hybrid transform with TOPOT_TABLE): K samples of kbar on
+    // a + i h; K + 1 padded FP32 pairs (ends (y_0, 0), (y_{K-1}, 0); segment r:
+    // (y_r + d_r / 2, d_r)) and the FP64 samples
+    const float2* ktab;
+    const double* ktab64;
+    int ktab_k;
+    double ktab_a, ktab_h;
 };
 
 __device__ __forceinline__ int orthant_of(const double* xi, int n) {

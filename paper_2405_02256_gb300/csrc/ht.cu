@@ -491,6 +491,169 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
     }
 }
 
+// ---- tabulated kernel -------------------------------------------------------------------------
+// kbar is the piecewise-linear interpolant of K samples y_i = kbar(a + i h), constant outside
+// [a, b]; kappa is its derivative, the segment slope on [a + i h, a + (i + 1) h) and zero
+// outside [a, b).
+
+__device__ __forceinline__ double table_kbar64(const EvalPlan& P, double s) {
+    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
+    const int K = P.ktab_k;
+    if (u < 0.0) return P.ktab64[0];
+    if (!(u < (double)(K - 1))) return P.ktab64[K - 1];
+    const double fi = floor(u);
+    const int i = (int)fi;
+    const double y0 = P.ktab64[i];
+    return __dadd_rn(y0, __dmul_rn(__dsub_rn(u, fi), __dsub_rn(P.ktab64[i + 1], y0)));
+}
+
+__device__ __forceinline__ double table_kappa64(const EvalPlan& P, double s) {
+    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
+    if (!(u >= 0.0 && u < (double)(P.ktab_k - 1))) return 0.0;
+    const int i = (int)floor(u);
+    return __ddiv_rn(__dsub_rn(P.ktab64[i + 1], P.ktab64[i]), P.ktab_h);
+}
+
+// FP32: the position p = u + 1/2 is clamped to [0, K] by a saturating FMA on the scaled
+// position p / K, and rounded to the nearest integer j by one FMA that adds 1.5 * 2^23
+// (j lands in the low mantissa bits: no conversion instruction).  The padded table holds
+// K + 1 pairs: entry j = r + 1 (0 <= r <= K - 2) is (y_r + d_r / 2, d_r), d_r = y_{r+1} - y_r,
+// and the two ends are (y_0, 0) and (y_{K-1}, 0).  With g = p - j in [-1/2, 1/2]:
+// kbar = Y + g D and kappa = D / h, constant ends and zero slope outside [a, b) included.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23; bits 0x4B400000
+constexpr int kRoundMagicBits = 0x4B400000;
+
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// ps = p / K in [0, 1]
+__device__ __forceinline__ float2 table_entry(const float2* tab, float ps, float Kf, float& g) {
+    const float t = fmaf(ps, Kf, kRoundMagic);
+    const float j = __fsub_rn(t, kRoundMagic);
+    g = fmaf(ps, Kf, -j);
+    return tab[__float_as_int(t) - kRoundMagicBits];
+}
+
+constexpr int kTabStage = 2048;      // float4 slots of the stage / reduction area (32 KB)
+constexpr int kTabMaxK = 16384;      // samples (K + 1 padded FP32 pairs, 128 KB)
+
+// Forward (ADJ = false: one sum per direction) or adjoint (n sums) with the tabulated
+// kernel, FP32 compensated.  The scaled position of a term is formed directly,
+// p / K = v0 + sum_k c_k w'_k (saturated) with the staged integers c_k = 2 i_k - (m_k - 1),
+// w'_k = xi_k / (2 (m_k - 1) h K) and v0 = (1/2 - a / h) / K; the kernel value is then
+// one rounding FMA, one shared-memory load and two FMAs.  Blocks of four points are summed by FMA and added
+// with compensation; the rounds are padded with zero-value points.
+template <int NDIM, int DL, bool ADJ, typename Tval>
+__global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev t, double* part) {
+    constexpr int NC = ADJ ? NDIM : 1;
+    constexpr int TDH = 32 * DL;
+    constexpr int NO = 1 << NDIM;
+    constexpr int SUB = ADJ ? kTabStage / 2 : kTabStage;   // staged points per round
+    static_assert(sizeof(double) * kHtWarps * TDH * NC <= sizeof(float4) * kTabStage, "reduction buffer");
+    extern __shared__ __align__(16) unsigned char smem_tab[];
+    float4* A = reinterpret_cast<float4*>(smem_tab);        // (c0, c1, c2, value)
+    float4* X = A + SUB;                                     // adjoint: (x0, x1, x2)
+    double(*red)[TDH * NC] = reinterpret_cast<double(*)[TDH * NC]>(smem_tab);
+    float2* tab = reinterpret_cast<float2*>(smem_tab + sizeof(float4) * kTabStage);
+    __shared__ long long sh_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long nitems = P.ctl[2];
+    const int K = P.ktab_k;
+    for (int i = tid; i <= K; i += kHtBlock) tab[i] = P.ktab[i];
+    const float Kf = (float)K;
+    const float inv_h = (float)(1.0 / P.ktab_h);
+    const float v0 = (float)((0.5 - P.ktab_a / P.ktab_h) / (double)K);
+
+    while (true) {
+        __syncthreads();
+        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= nitems) break;
+        int tile;
+        const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        float wt[DL][3];
+#pragma unroll
+        for (int j = 0; j < DL; ++j) {
+            HtDir hd;
+            ht_dir<NDIM, TOPOT_TABLE>(P, it, tile * TDH + j * 32 + lane, hd);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                wt[j][k] = k < NDIM ? (float)(hd.xi[k] / (2.0 * (double)(it.I->m[k] - 1) * P.ktab_h * (double)K)) : 0.0f;
+        }
+        float acc[DL][NC], cmp[DL][NC];
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
+
+        for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
+            const int cnt = (int)min((long long)SUB, it.e_end - e0);
+            const int cnt_pad = (cnt + kHtWarps * 4 - 1) / (kHtWarps * 4) * (kHtWarps * 4);
+            __syncthreads();
+            ht_stage<NDIM, TOPOT_TABLE, ADJ, Tval>(t, it, e0, cnt, A, X);
+            for (int i = cnt + tid; i < cnt_pad; i += kHtBlock) {
+                A[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (ADJ) X[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            __syncthreads();
+            const int per = cnt_pad / kHtWarps;
+            const int ws = warp * per, we = ws + per;
+            for (int e = ws; e < we; e += 4) {
+                float blk[DL][NC];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 q = A[e + u];
+                    float xs[3] = {0.0f, 0.0f, 0.0f};
+                    if (ADJ) {
+                        const float4 x = X[e + u];
+                        xs[0] = x.x;
+                        xs[1] = x.y;
+                        xs[2] = x.z;
+                    }
+                    const float vw = ADJ ? q.w * inv_h : q.w;
+#pragma unroll
+                    for (int j = 0; j < DL; ++j) {
+                        float ps = fmaf(q.x, wt[j][0], v0);
+                        if (NDIM == 3) ps = fmaf(q.y, wt[j][1], ps);
+                        ps = fma_sat(NDIM == 3 ? q.z : q.y, wt[j][NDIM - 1], ps);
+                        float g;
+                        const float2 te = table_entry(tab, ps, Kf, g);
+                        if (!ADJ) {
+                            const float kv = fmaf(g, te.y, te.x);
+                            blk[j][0] = u == 0 ? q.w * kv : fmaf(q.w, kv, blk[j][0]);
+                        } else {
+                            const float tk = vw * te.y;
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) blk[j][c] = u == 0 ? tk * xs[c] : fmaf(tk, xs[c], blk[j][c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < DL; ++j)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) kahan_add(acc[j][c], cmp[j][c], blk[j][c]);
+            }
+        }
+        __syncthreads();   // red aliases the stage
+#pragma unroll
+        for (int j = 0; j < DL; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] - (double)cmp[j][c];
+        __syncthreads();
+        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            part[item * (TDH * NC) + i] = s;
+        }
+    }
+}
+
 // ---- forward, plain FP64 ---------------------------------------------------------------------
 
 template <int NDIM, int KERNEL, typename Tval>
@@ -556,6 +719,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f64(EvalPlan P, TablesDev t, do
                     acc[1] += q.w * cs;
                 } else if (KERNEL == TOPOT_SINE) {
                     acc[0] += q.w * cos(s);
+                } else if (KERNEL == TOPOT_TABLE) {
+                    acc[0] += q.w * table_kbar64(P, s);
                 } else {
                     acc[0] += q.w * j0(s);
                 }
@@ -867,7 +1032,11 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f64(EvalPlan P, TablesDev t
                         acc[NDIM + k] += q.w * sn * xs[k];
                     }
                 } else {
-                    const double kv = KERNEL == TOPOT_LAPLACE ? exp(s) : (KERNEL == TOPOT_SINE ? sin(s) : -j1(s));
+                    double kv;
+                    if (KERNEL == TOPOT_LAPLACE) kv = exp(s);
+                    else if (KERNEL == TOPOT_SINE) kv = sin(s);
+                    else if (KERNEL == TOPOT_TABLE) kv = table_kappa64(P, s);
+                    else kv = -j1(s);
 #pragma unroll
                     for (int k = 0; k < NDIM; ++k) acc[k] += q.w * kv * xs[k];
                 }
@@ -998,6 +1167,38 @@ static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precis
     return cudaGetLastError();
 }
 
+template <int NDIM, int DL, bool ADJ, typename Tval>
+static cudaError_t launch_ht_table_k(const EvalPlan& P, const TablesDev& t, int grid, double* part,
+                                     cudaStream_t st) {
+    auto kern = k_ht_table_f32<NDIM, DL, ADJ, Tval>;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float4) * kTabStage + sizeof(float2) * (kTabMaxK + 1)));
+    if (attr != cudaSuccess) return attr;
+    if (P.ktab_k < 2 || P.ktab_k > kTabMaxK) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float4) * kTabStage + sizeof(float2) * (size_t)(P.ktab_k + 1);
+    kern<<<grid, kHtBlock, smem, st>>>(P, t, part);
+    return cudaGetLastError();
+}
+
+template <int NDIM, typename Tval>
+static cudaError_t launch_ht_table(const EvalPlan& P, const TablesDev& t, int precision, bool adjoint, int dl,
+                                   int grid, double* part, cudaStream_t st) {
+    if (precision == TOPOT_FP64) {
+        if (adjoint) k_ht_adj_f64<NDIM, TOPOT_TABLE, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+        else k_ht_f64<NDIM, TOPOT_TABLE, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+        return cudaGetLastError();
+    }
+    switch (dl) {
+        case 1: return adjoint ? launch_ht_table_k<NDIM, 1, true, Tval>(P, t, grid, part, st)
+                               : launch_ht_table_k<NDIM, 1, false, Tval>(P, t, grid, part, st);
+        case 2: return adjoint ? launch_ht_table_k<NDIM, 2, true, Tval>(P, t, grid, part, st)
+                               : launch_ht_table_k<NDIM, 2, false, Tval>(P, t, grid, part, st);
+        case 4: return adjoint ? launch_ht_table_k<NDIM, 4, true, Tval>(P, t, grid, part, st)
+                               : launch_ht_table_k<NDIM, 4, false, Tval>(P, t, grid, part, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int NDIM, typename Tval>
 static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint,
                                int dl, int grid, double* part, cudaStream_t st) {
@@ -1006,6 +1207,7 @@ static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel
         case TOPOT_FOURIER: return launch_ht_k<NDIM, TOPOT_FOURIER, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         case TOPOT_BESSEL: return launch_ht_k<NDIM, TOPOT_BESSEL, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         case TOPOT_SINE: return launch_ht_k<NDIM, TOPOT_SINE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        case TOPOT_TABLE: return launch_ht_table<NDIM, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         default: return cudaErrorInvalidValue;
     }
 }

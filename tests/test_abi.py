@@ -51,3 +51,20 @@ def test_last_error_without_gpu(lib_path):
     assert st == 1 and b"n must be 2 or 3" in L.topot_last_error()
     st = L.tables_create(0, 2, shapes, offs, 1, 7, ctypes.byref(h))
     assert st == 1 and b"construction" in L.topot_last_error()
+
+
+def test_kernel_table_validation_without_gpu(lib_path):
+    """kernel_table_create rejects bad samples and ranges before any CUDA call."""
+    from paper_2405_02256_gb300 import binding
+    L = binding.load(lib_path)
+    h = ctypes.c_void_p()
+    y = (ctypes.c_double * 3)(1.0, 2.0, 3.0)
+    assert L.kernel_table_create(y, 1, 0.0, 1.0, ctypes.byref(h)) == 1
+    assert b"K" in L.topot_last_error()
+    assert L.kernel_table_create(y, 3, 1.0, 1.0, ctypes.byref(h)) == 1
+    assert L.kernel_table_create(y, 3, 0.0, float("inf"), ctypes.byref(h)) == 1
+    bad = (ctypes.c_double * 3)(1.0, float("nan"), 3.0)
+    assert L.kernel_table_create(bad, 3, 0.0, 1.0, ctypes.byref(h)) == 1
+    assert b"non-finite" in L.topot_last_error()
+    assert L.hybrid_transform_table(None, None, 0, None, 1, 0, None, None) == 1
+    L.kernel_table_free(None)
