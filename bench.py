@@ -396,6 +396,21 @@ def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_
                        "ms": ms, "terms_per_s": terms / (ms / 1e3)}
     del o_sine
 
+    # f3: a tabulated kernel, kbar given by K samples (piecewise linear, constant ends);
+    # here K = 1024 samples of sin(2 s) + 0.3 s^2 on [-R, R]
+    tab_rows = {}
+    for K in (64, 1024):
+        sk = -R2 + 2 * R2 / (K - 1) * np.arange(K)
+        kt = tb.KernelTable(np.sin(2.0 * sk) + 0.3 * sk * sk, -R2, R2)
+        o_tab = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
+        ms = _time_cuda(lambda: tb.hybrid_transform(tabs, kt, dirs_ht, "fp32c", out=o_tab), reps=1)
+        tab_rows[f"K{K}_ms"] = ms
+        tab_rows[f"K{K}_terms_per_s"] = terms / (ms / 1e3)
+        del o_tab
+        kt.free()
+    rows["table_2d"] = {"workload": "same tables; 4096 dirs, kbar tabulated by K samples on [-R, R], FP32C",
+                        **tab_rows}
+
     # f1: exact representations (T, E) and (T', E') at 4 directions per image, and their
     # evaluation at 4096 arbitrary thresholds
     tabs.sync()                                   # sizes on the host (the step rebuilt the tables)
