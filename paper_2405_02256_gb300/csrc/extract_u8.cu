@@ -44,9 +44,9 @@ template <> struct U8Cfg<2> {
     static constexpr int MINB = 2;      // resident blocks per SM (registers <= 64)
 };
 template <> struct U8Cfg<3> {
-    static constexpr int B = 256;
+    static constexpr int B = 512;
     static constexpr int STRIP = 4;
-    static constexpr int MINB = 4;      // registers <= 64 (a few spills; measured faster than 3 blocks)
+    static constexpr int MINB = 2;      // registers <= 64
 };
 
 constexpr int kPadB = 16;               // staged row interior starts 16 bytes in
