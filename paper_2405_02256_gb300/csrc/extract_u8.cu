@@ -69,10 +69,9 @@ template <int NDIM> struct U8Layout {
     static constexpr int OFF_WEX = OFF_WSUM + NW * 32;        // [NW][8] words
     static constexpr int OFF_TOT = OFF_WEX + NW * 32;         // [8] words
     static constexpr int OFF_PREF = OFF_TOT + 32;             // [SEG] long long
-    static constexpr int OFF_RED = OFF_PREF + 8 * SEG;        // [1 + NO] int
     static constexpr int OFF_OUT = kHdr;                       // [SEG * CAP] words
     static constexpr int OFF_STAGE = OFF_OUT + 4 * SEG * CAP;
-    static_assert(OFF_RED + 4 * (1 + NO) <= kHdr, "shared-memory header too small");
+    static_assert(OFF_PREF + 8 * SEG <= kHdr, "shared-memory header too small");
     static_assert(CAP <= 65536, "tile-local vertex index must fit 16 bits");
 };
 
