@@ -45,6 +45,13 @@ HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.1e6 + 4.6e6) / 8, "ht_fourier": (95
                            "ht_bessel": (98.0e6 + 4.4e6) / 8}
 
 
+def bench_config(n_img: int, side: int, world: int) -> dict:
+    """The workload both arms report (the reference arm times the CPU oracle on samples of it)."""
+    return {"workload": WORKLOAD, "images": n_img, "side": side, "ect_dirs": D_ECT, "thresholds": T_ECT,
+            "ht_dirs": D_HT, "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def make_images(count: int, side: int):
     from paper_2405_02256_gb300 import synth
     return [synth.grf((side, side), ELL, seed=1000 + b) for b in range(count)]
@@ -299,9 +306,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8 tables / fp32c hybrid", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images": n_img, "side": args.side, "ect_dirs": D_ECT,
-                   "thresholds": T_ECT, "ht_dirs": D_HT, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": bench_config(n_img, args.side, world),
         "phases_ms": dict(zip(names, [float(x) for x in ph_ms])),
         "ect_dirs_per_s": n_img * D_ECT * world / (ph_ms[1] / 1e3),
         "ect_updates_per_s": ect_updates / (ph_ms[1] / 1e3),
@@ -584,8 +589,8 @@ def run_reference(args):
     imgs = make_images(1, SIDE)
     _, dirs_ht = make_dirs()
     vals = []
-    for _ in range(args.warmup):
-        pass
+    for _ in range(args.warmup):   # untimed: a short sample (tables of the image, a few directions)
+        cpu_baseline(imgs[0], dirs_ht, budget_s=1.0)
     t0 = time.time()
     per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     samples = []
@@ -598,7 +603,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD},
+           "config": bench_config(args.images, args.side, world),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples[0]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
