@@ -544,8 +544,8 @@ constexpr int kTabMaxK = 16384;      // samples (K + 1 padded FP32 pairs, 128 KB
 // kernel, FP32 compensated.  The scaled position of a term is formed directly,
 // p / K = v0 + sum_k c_k w'_k (saturated) with the staged integers c_k = 2 i_k - (m_k - 1),
 // w'_k = xi_k / (2 (m_k - 1) h K) and v0 = (1/2 - a / h) / K; the kernel value is then
-// one rounding FMA, one shared-memory load and two FMAs.  Blocks of four points are summed by FMA and added
-// with compensation; the rounds are padded with zero-value points.
+// one rounding FMA, one shared-memory load and two FMAs.  Blocks of four points are summed
+// by FMA and added with compensation; the rounds are padded with zero-value points.
 template <int NDIM, int DL, bool ADJ, typename Tval>
 __global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev t, double* part) {
     constexpr int NC = ADJ ? NDIM : 1;
@@ -581,8 +581,10 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev
             HtDir hd;
             ht_dir<NDIM, TOPOT_TABLE>(P, it, tile * TDH + j * 32 + lane, hd);
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                wt[j][k] = k < NDIM ? (float)(hd.xi[k] / (2.0 * (double)(it.I->m[k] - 1) * P.ktab_h * (double)K)) : 0.0f;
+            for (int k = 0; k < 3; ++k) {
+                const double scale = 2.0 * (double)(it.I->m[k] - 1) * P.ktab_h * (double)K;
+                wt[j][k] = k < NDIM ? (float)(hd.xi[k] / scale) : 0.0f;
+            }
         }
         float acc[DL][NC], cmp[DL][NC];
 #pragma unroll
@@ -628,7 +630,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev
                         } else {
                             const float tk = vw * te.y;
 #pragma unroll
-                            for (int c = 0; c < NC; ++c) blk[j][c] = u == 0 ? tk * xs[c] : fmaf(tk, xs[c], blk[j][c]);
+                            for (int c = 0; c < NC; ++c)
+                                blk[j][c] = u == 0 ? tk * xs[c] : fmaf(tk, xs[c], blk[j][c]);
                         }
                     }
                 }
