@@ -272,8 +272,8 @@ TOPOT_API topot_status hybrid_transform_noalloc(const topot_tables* t, topot_ker
  *   u = (s - s_min) / h, i = floor(u), f = u - i:  kbar(s) = y_i + f (y_{i+1} - y_i)
  *   for 0 <= u < K - 1;  y_0 for u < 0;  y_{K-1} for u >= K - 1,
  * and kappa = kbar' the step function (y_{i+1} - y_i) / h on [s_min + i h,
- * s_min + (i + 1) h), zero outside [s_min, s_max).  2 <= K <= 16384, finite samples,
- * s_min < s_max (finite), else INVALID_ARG.  The handle owns device copies on the
+ * s_min + (i + 1) h), zero outside [s_min, s_max).  2 <= K <= 16384, finite samples of
+ * magnitude <= 1e37 (the FP32 table range), s_min < s_max (finite), else INVALID_ARG.  The handle owns device copies on the
  * current device (for FP32C, K + 1 FP32 pairs: (y_0, 0), (y_r + d_r / 2, d_r) per
  * segment r with d_r = y_{r+1} - y_r, (y_{K-1}, 0); for FP64 the samples); free it with
  * kernel_table_free after the last call that uses it has completed. */

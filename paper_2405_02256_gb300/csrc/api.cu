@@ -666,8 +666,12 @@ topot_status kernel_table_create(const double* h_values, int K, double s_min, do
         return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: need 2 <= K <= 16384 samples");
     if (!std::isfinite(s_min) || !std::isfinite(s_max) || !(s_min < s_max))
         return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: need finite s_min < s_max");
-    for (int i = 0; i < K; ++i)
+    for (int i = 0; i < K; ++i) {
         if (!std::isfinite(h_values[i])) return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: non-finite sample");
+        // the FP32 table holds samples, half-sums and differences: keep them all finite
+        if (std::fabs(h_values[i]) > 1e37)
+            return fail(TOPOT_ERR_INVALID_ARG, "kernel_table_create: |sample| above 1e37 (FP32 table range)");
+    }
     topot_ktable* k = new (std::nothrow) topot_ktable;
     if (!k) return fail(TOPOT_ERR_OOM, "kernel_table_create: host allocation");
     k->K = K;

@@ -66,5 +66,8 @@ def test_kernel_table_validation_without_gpu(lib_path):
     bad = (ctypes.c_double * 3)(1.0, float("nan"), 3.0)
     assert L.kernel_table_create(bad, 3, 0.0, 1.0, ctypes.byref(h)) == 1
     assert b"non-finite" in L.topot_last_error()
+    big = (ctypes.c_double * 3)(1.0, 3e37, 3.0)
+    assert L.kernel_table_create(big, 3, 0.0, 1.0, ctypes.byref(h)) == 1
+    assert b"1e37" in L.topot_last_error()
     assert L.hybrid_transform_table(None, None, 0, None, 1, 0, None, None) == 1
     L.kernel_table_free(None)
