@@ -24,12 +24,14 @@ def _ragged(count, seed, lo=28, hi=160):
     return [synth.blurred_noise(s, 2.0, seed=seed * 1000 + i) for i, s in enumerate(shapes)]
 
 
-def _pipeline(tb, imgs, ect_dirs, ht_dirs, T=64):
+def _pipeline(tb, imgs, ect_dirs, ht_dirs, T=64, ktab=None):
     batch = tb.pack_images(imgs)
     R = synth.image_radius(2)
+    hybrid = [("laplace", ht_dirs, "fp32c"), ("fourier", ht_dirs, "fp32c")]
+    if ktab is not None:
+        hybrid.append((ktab, ht_dirs, "fp32c"))
     pipe = tb.Pipeline(batch.shapes, batch.offsets, batch.pixels.numel(),
-                       ect=(ect_dirs, -R, R, T), radon=(ect_dirs, -R, R, T),
-                       hybrid=[("laplace", ht_dirs, "fp32c"), ("fourier", ht_dirs, "fp32c")])
+                       ect=(ect_dirs, -R, R, T), radon=(ect_dirs, -R, R, T), hybrid=hybrid)
     return pipe, batch
 
 
@@ -38,7 +40,9 @@ def test_graph_replay_matches_eager_and_follows_new_pixels(tb):
     imgs_b = [synth.blurred_noise(im.shape, 2.0, seed=7000 + i) for i, im in enumerate(imgs_a)]
     ect_dirs = torch.from_numpy(synth.circle_dirs(64)).cuda()
     ht_dirs = torch.from_numpy(synth.circle_dirs(256)).cuda()
-    pipe, batch_a = _pipeline(tb, imgs_a, ect_dirs, ht_dirs)
+    knots = np.linspace(-0.8, 0.8, 129)
+    ktab = tb.KernelTable(np.exp(-4.0 * knots * knots), -0.8, 0.8)   # a tabulated kernel in the graph too
+    pipe, batch_a = _pipeline(tb, imgs_a, ect_dirs, ht_dirs, ktab=ktab)
     batch_b = tb.pack_images(imgs_b)
     pipe.pixels.copy_(batch_a.pixels)
     pipe.capture()
@@ -51,6 +55,7 @@ def test_graph_replay_matches_eager_and_follows_new_pixels(tb):
         assert torch.equal(pipe.radon_out, tb.radon(eager, ect_dirs, -R, R, 64))
         assert torch.equal(pipe.hybrid_out[0], tb.hybrid_transform(eager, "laplace", ht_dirs))
         assert torch.equal(pipe.hybrid_out[1], tb.hybrid_transform(eager, "fourier", ht_dirs))
+        assert torch.equal(pipe.hybrid_out[2], tb.hybrid_transform(eager, ktab, ht_dirs))
 
 
 def test_ragged_batch_against_oracle(tb):
