@@ -41,8 +41,8 @@ FP64_SAMPLE_DIRS = 128
 # DRAM bytes (read + write) per image of one FP32C hybrid launch, from the ncu capture of
 # the 8-image case in profiles/k_ht_f32_8x2048_grf.md (the tables are read once per work
 # item, so the traffic grows with the number of images)
-HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.1e6 + 4.6e6) / 8, "ht_fourier": (95.0e6 + 5.1e6) / 8,
-                           "ht_bessel": (98.0e6 + 4.4e6) / 8}
+HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.1e6 + 4.5e6) / 8, "ht_fourier": (92.1e6 + 4.9e6) / 8,
+                           "ht_bessel": (97.4e6 + 4.3e6) / 8}
 
 
 def bench_config(n_img: int, side: int, world: int) -> dict:

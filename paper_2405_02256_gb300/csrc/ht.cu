@@ -307,22 +307,23 @@ __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_
 }
 
 // Packed evaluation of staged points [ws, we) for NPR direction pairs.  Terms are
-// summed by FMA in blocks of BLK points (8, or 4 for Fourier whose MUFU sin/cos carry
-// more error), and each block sum is added with compensation: a block adds at most
-// BLK eps of its terms' magnitudes, the compensated sum 2 eps.
+// summed by FMA in blocks of 8 points, and each block sum is added with compensation: a
+// block adds at most 8 eps of its terms' magnitudes, the compensated sum 2 eps.  For
+// Fourier and sine the pairs on MUFU sin / cos (odd pairs), whose evaluation takes most of
+// the error budget, close their block every 4 points.
 template <int NDIM, int KERNEL, int NPR, int PATH>
 __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we, const float2 (&w)[NPR][3],
                                                 float2 (&s2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1],
                                                 float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
-    constexpr int BLK = (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE) ? 4 : 8;
-    // [ws, we) is a multiple of BLK long (rounds are padded with zero-value points); each
+    constexpr bool SPLIT = KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE;
+    // [ws, we) is a multiple of 8 long (rounds are padded with zero-value points); each
     // block is summed in two interleaved chains (even / odd points) to halve the
     // dependency depth, then added with compensation.
-    for (int e = ws; e < we; e += BLK) {
+    for (int e = ws; e < we; e += 8) {
         float2 ba[NPR][NC], bb[NPR][NC];
 #pragma unroll
-        for (int u = 0; u < BLK; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const float4 qa = A[2 * (e + u)];
             const float4 qb = A[2 * (e + u) + 1];
             const float2 c0 = make_float2(qa.x, qa.y), c1 = make_float2(qa.z, qa.w);
@@ -334,13 +335,20 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
                 if (NDIM == 3) z = fma2(c2, w[pq][2], z);
                 float2 k[2];
                 kernel_pair<KERNEL, PATH>(z, k, (pq & 1) == 1);
+                const int ub = (SPLIT && (pq & 1)) ? (u & 3) : u;   // position in the pair's block
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    if (u == 0) ba[pq][c] = mul2(v2, k[c]);
-                    else if (u == 1) bb[pq][c] = mul2(v2, k[c]);
-                    else if (u & 1) bb[pq][c] = fma2(v2, k[c], bb[pq][c]);
+                    if (ub == 0) ba[pq][c] = mul2(v2, k[c]);
+                    else if (ub == 1) bb[pq][c] = mul2(v2, k[c]);
+                    else if (ub & 1) bb[pq][c] = fma2(v2, k[c], bb[pq][c]);
                     else ba[pq][c] = fma2(v2, k[c], ba[pq][c]);
                 }
+            }
+            if (SPLIT && u == 3) {
+#pragma unroll
+                for (int pq = 1; pq < NPR; pq += 2)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) kahan2_add(s2[pq][c], n2[pq][c], add2(ba[pq][c], bb[pq][c]));
             }
         }
 #pragma unroll
