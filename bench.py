@@ -578,7 +578,8 @@ def cpu_baseline(img, dirs_ht, budget_s: float = 20.0):
         ndirs += 1
     t_ht = time.time() - t1
     return {"value": terms / t_ht, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 image of {SIDE}x{SIDE}: tables in {t_tables:.1f} s, then {ndirs} directions x 3 kernels "
+            "sample": f"1 image of {'x'.join(map(str, img.shape))}: tables in {t_tables:.1f} s, then {ndirs} "
+                      f"directions x 3 kernels "
                       f"({terms} terms) in {t_ht:.1f} s"}
 
 
