@@ -82,9 +82,8 @@ def test_thresholds_on_the_lattice(shape, T, a, b):
 
 
 def test_without_the_filter_some_fp32_bins_would_be_wrong():
-    # the same lattice-aligned case with every decision taken in FP32: points whose u rounds
-    # onto an integer while the FP64 dot product sits one ulp on the other side of t_j
-    dirs = [np.eye(2)[0], -np.eye(2)[0], np.eye(2)[1], np.ones(2), np.ones(2) / 2,
-            np.array([0.5, 0.25]), np.array([1.0, -1.0])]
+    # random directions with every decision taken in FP32: some points lie closer to a
+    # threshold than the FP32 error of u, and their FP32 bin differs from the FP64 one
+    dirs = list(np.random.default_rng(17).normal(size=(100, 2)))
     with pytest.raises(AssertionError):
-        _check((21, 33), dirs, 129, -1.0, 1.0, no_filter=True)
+        _check((64, 96), dirs, 512, no_filter=True)
