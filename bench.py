@@ -278,8 +278,10 @@ def run_gpu(args):
     # operation counts 2, MUFU operations are not counted; the average over the MUFU and
     # polynomial halves for Fourier), and issued instructions per (point, direction)
     # update of the ECT kernel; both counted from the kernel source
-    fp32_ops = {"ht_laplace": 3.5, "ht_fourier": 9.5, "ht_bessel": 7.5}
-    ect_instr = 16.0
+    fp32_ops = {"ht_laplace": 3.5, "ht_fourier": 9.5, "ht_bessel": 8.5}
+    # warp instructions per 32 (point, direction) updates of k_hist, from its ncu
+    # capture (instructions executed / updates x 32)
+    ect_instr = 23.0
     if names[dom] == "extract":
         achieved = ext_bytes / (ph_ms[dom] / 1e3) / 1e9
         roof = {"kernel": "k_extract", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -301,7 +303,9 @@ def run_gpu(args):
                 "terms_per_s": term_rate, "fp32_lane_ops_per_term": fp32_ops[nm],
                 "peak_source": "152 SMs x 128 FP32 lanes x max SM clock (recipe unit counts)"}
 
-    launches_per_step = 1 + 4 + 4 * len(KERNELS)
+    # extraction 1; ECT: direction prep, plan, histogram, finish; each hybrid transform:
+    # direction prep, plan, packed and wide-range launches, combine
+    launches_per_step = 1 + 4 + 5 * len(KERNELS)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -224,10 +224,18 @@ TOPOT_API topot_status radon_exact_eval(int nrep, int64_t cap, const double* d_T
  * Hybrid transforms (Section 2.2; closed form and sign of Lemma 3.1)
  * ---------------------------------------------------------------------------
  *   HT(xi) = - sum_v Delta^ord_eps(v) kbar(<xi, v>) = sum_v Delta_eps(v) kbar(<xi, v>)
- * (= -int kappa(t) R(xi, t) dt).  d_out: FP64 [B][D] (LAPLACE, BESSEL) or
- * [B][D][2] (FOURIER: re, im).  Deterministic for a given tuning.
- * Accuracy (FP32C): |HT - exact| <= 1e-6 sum_v |Delta kbar| for the documented
- * ranges |<xi, v>| <= pi. */
+ * (= -int kappa(t) R(xi, t) dt).  d_out: FP64 [B][D] (LAPLACE, BESSEL, SINE) or
+ * [B][D][2] (FOURIER: re, im).  Deterministic for a given tuning and direction set.
+ * Accuracy, with M = sum_k |xi_k| / 2 >= |<xi, v>|:
+ *   FP32C: |HT - exact| <= 1e-6 sum_v |Delta kbar(<xi, v>)| (complex modulus for FOURIER)
+ *     for every finite xi with M <= 1e6; LAPLACE needs M <= 300 and returns NaN beyond.
+ *     The terms are kbar(s) - kbar(0) (the constant cancels: sum_v Delta_eps(v) = 0),
+ *     so transforms much smaller than that bound (small |xi|) keep their relative
+ *     accuracy; tiles with M above 1 (LAPLACE), 1.75 (FOURIER, SINE) or 2 (BESSEL)
+ *     form <xi, v> in FP64 and reduce it modulo 2 pi before the FP32 evaluation.
+ *     Beyond M ~ 1e6 the FP64 rounding of <xi, v> (2^-53 |<xi, v>|) dominates.
+ *   FP64: plain FP64 terms and sums (error of the order of 1e-15 sum_v |Delta kbar|);
+ *     LAPLACE overflows (inf or NaN) once some <xi, v> exceeds ~709. */
 TOPOT_API topot_status hybrid_transform(const topot_tables* t, topot_kernel kernel,
                               topot_precision precision, const double* d_dirs, int D,
                               int per_image_dirs, double* d_out, void* stream);
@@ -238,7 +246,8 @@ TOPOT_API topot_status hybrid_transform(const topot_tables* t, topot_kernel kern
  * Lemma 3.2).  d_gout is shaped like d_out of hybrid_transform; d_gdirs like d_dirs
  * (FP64).  For FOURIER, gout = (g_re, g_im) and the result is
  * g_re d Re/d xi + g_im d Im/d xi.  With per_image_dirs = 0 the gradients of all
- * images are summed per direction. */
+ * images are summed per direction.  Accuracy (FP32C): 2e-6 of sum_v |Delta kappa x_k|
+ * per component over the ranges of hybrid_transform (same paths, same LAPLACE limit). */
 TOPOT_API topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel kernel,
                                    topot_precision precision, const double* d_dirs, int D,
                                    int per_image_dirs, const double* d_gout,

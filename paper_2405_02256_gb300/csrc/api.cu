@@ -267,6 +267,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         I.segs_per_row = (m0 + I.W - 1) / I.W;
         I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
         tiles += (long long)I.tiles_per_plane * I.m[2];
+        for (int k = 0; k < kMaxDim; ++k) I.inv2m[k] = I.m[k] > 1 ? 0.5 / (double)(I.m[k] - 1) : 0.0;
         I.div0 = make_fastdiv((uint32_t)m0);
         I.div1 = make_fastdiv((uint32_t)m1);
         I.div_spr = make_fastdiv((uint32_t)std::max(1, I.spr));

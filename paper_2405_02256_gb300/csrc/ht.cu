@@ -14,9 +14,20 @@
 // per lane; at the end of an item the eight warps' (sum - compensation) are added in
 // FP64 in warp order and stored as the item's partial; k_ht_combine adds the chunk
 // partials of each direction in chunk order in FP64.  The result is deterministic.
+// The forward FP32C kernels sum kbar(s) - kbar(0) rather than kbar(s) for the kernels
+// with a constant term (Fourier's imaginary part cos s, sine, Bessel): the constant
+// drops out of the closed form because sum_v Delta_eps(v) = 0 over a whole table, and
+// without it a term stays small where kbar(s) is close to kbar(0) (cos s - 1 = -w q(w),
+// J0 - 1 = -y q(y) on the polynomial paths), so small transforms keep their accuracy.
 // Laplace uses e^s = e^M e^{s - M} with M = sum_k |xi_k| / 2 = max_v s_v:
 // s - M = sum_k (|xi_k| / (m_k - 1)) q_k with integer q_k <= 0, so every FP32 exponent
-// is <= 0 (no overflow) and is a sum of non-positive terms (no cancellation).
+// is <= 0 (no overflow) and is a sum of non-positive terms (no cancellation); for
+// M <= 40 no term underflows either, beyond that the scalar path rescales each round of
+// staged points by its own largest term.
+// Arguments: the packed paths form <xi, v> in FP32 (absolute error <= 3 * 2^-24 M,
+// M <= 2); the scalar path does the same up to |s| <= 1.75 (Fourier, sine) or 2
+// (Bessel) and beyond forms s in FP64 and reduces it modulo 2 pi in FP64 before the
+// FP32 evaluation, so its error does not grow with |s|.
 // FP64: the canonical FP64 dot product and library FP64 kernels, plain FP64 sums.
 #include <algorithm>
 
@@ -39,57 +50,182 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float term) {
     sum = t;
 }
 
-// J0 for |x| <= 2 from its ascending series (Abramowitz & Stegun 9.1.10):
-// J0(x) = sum_k (-y)^k / (k!)^2, y = x^2 / 4 <= 1; truncation after k = 9 < 1e-13.
-__device__ __forceinline__ float j0_series_f(float x) {
-    const float y = 0.25f * x * x;
-    float p = 1.0f / 131681894400.0f;            // k = 9: 1 / (9!)^2
-    p = fmaf(p, -y, 1.0f / 1625702400.0f);        // k = 8
-    p = fmaf(p, -y, 1.0f / 25401600.0f);          // k = 7
-    p = fmaf(p, -y, 1.0f / 518400.0f);            // k = 6
-    p = fmaf(p, -y, 1.0f / 14400.0f);             // k = 5
-    p = fmaf(p, -y, 1.0f / 576.0f);               // k = 4
-    p = fmaf(p, -y, 1.0f / 36.0f);                // k = 3
-    p = fmaf(p, -y, 1.0f / 4.0f);                 // k = 2
-    p = fmaf(p, -y, 1.0f);                        // k = 1
-    return fmaf(p, -y, 1.0f);                     // k = 0
+// Range limits of the FP32 argument paths, by kernel (largest M = sum_k |xi_k| / 2 of a
+// tile, which bounds |<xi, v>|): beyond them the scalar path forms the argument in FP64.
+constexpr float kLaplaceM32 = 1.0f;     // Laplace: relative error of e^{s-M} <= 6 M 2^-24
+constexpr float kTrigM32 = 1.75f;       // Fourier, sine: polynomial and MUFU range
+constexpr float kBesselM32 = 2.0f;      // Bessel: polynomial range
+constexpr double kLaplaceMaxM = 300.0;  // FP32C Laplace: larger M gives NaN
+
+// ---- polynomial kernels -----------------------------------------------------------------------
+// Degree-d Chebyshev interpolants on [0, X] written in the power basis (constants derived
+// by gen_poly.py from the functions' own series; the listed bounds are the worst absolute
+// errors of the FP32 Horner evaluation).  One template serves a float and an f32x2 pair.
+__device__ __forceinline__ float fma_v(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 fma_v(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float splat(float c, float) { return c; }
+__device__ __forceinline__ float2 splat(float c, float2) { return make_float2(c, c); }
+
+template <int N, typename V>
+__device__ __forceinline__ V horner(const float (&c)[N], V x) {
+    V p = splat(c[N - 1], x);
+#pragma unroll
+    for (int k = N - 2; k >= 0; --k) p = fma_v(p, x, splat(c[k], x));
+    return p;
 }
 
-// J1 for |x| <= 2 (A&S 9.1.10): J1(x) = (x/2) sum_k (-y)^k / (k! (k+1)!).
-__device__ __forceinline__ float j1_series_f(float x) {
-    const float y = 0.25f * x * x;
-    float p = 1.0f / 1316818944000.0f;            // k = 9: 1 / (9! 10!)
-    p = fmaf(p, -y, 1.0f / 14631321600.0f);       // k = 8
-    p = fmaf(p, -y, 1.0f / 203212800.0f);         // k = 7
-    p = fmaf(p, -y, 1.0f / 3628800.0f);           // k = 6
-    p = fmaf(p, -y, 1.0f / 86400.0f);             // k = 5
-    p = fmaf(p, -y, 1.0f / 2880.0f);              // k = 4
-    p = fmaf(p, -y, 1.0f / 144.0f);               // k = 3
-    p = fmaf(p, -y, 1.0f / 12.0f);                // k = 2
-    p = fmaf(p, -y, 1.0f / 2.0f);                 // k = 1
-    p = fmaf(p, -y, 1.0f);                        // k = 0
-    return 0.5f * x * p;
+//   cos(sqrt w): X = 0.5625 (|z| <= 0.75), d = 3, 8e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
+template <typename V>
+__device__ __forceinline__ V cos_short(V w) {
+    constexpr float c[4] = {1.000000000e+00f, -4.999988973e-01f, 4.165696725e-02f, -1.361225732e-03f};
+    return horner(c, w);
+}
+template <typename V>
+__device__ __forceinline__ V cos_long(V w) {
+    constexpr float c[6] = {1.000000000e+00f, -4.999999702e-01f, 4.166659340e-02f, -1.388788689e-03f,
+                            2.473820496e-05f, -2.569863113e-07f};
+    return horner(c, w);
+}
+// sin z = z q(z^2): X = 0.5625 (|z| <= 0.75), d = 3, 4e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
+template <typename V>
+__device__ __forceinline__ V sinc_short(V w) {
+    constexpr float c[4] = {1.000000000e+00f, -1.666665524e-01f, 8.332253434e-03f, -1.953341998e-04f};
+    return horner(c, w);
+}
+template <typename V>
+__device__ __forceinline__ V sinc_long(V w) {
+    constexpr float c[6] = {1.000000000e+00f, -1.666666716e-01f, 8.333328180e-03f, -1.984049450e-04f,
+                            2.750829026e-06f, -2.361634976e-08f};
+    return horner(c, w);
+}
+// sin z = z q(z^2) for |z| <= 0.5: X = 0.25, d = 2, 1.5e-7 (relative)
+template <typename V>
+__device__ __forceinline__ V sinc_tiny(V w) {
+    constexpr float c[3] = {9.999998808e-01f, -1.666597277e-01f, 8.259218186e-03f};
+    return horner(c, w);
+}
+// cos z - 1 = w r(w), r = -(1 - cos sqrt w) / w (coefficients of gen_poly.py's cosm1q,
+// negated): X = 0.5625, d = 2: |w r| error 8e-8, relative 3.5e-7;  X = 3.0625, d = 4:
+// 1.1e-7, relative 1e-7
+template <typename V>
+__device__ __forceinline__ V cosm1_tiny(V w) {   // X = 0.25 (|z| <= 0.5), d = 2: relative 1.2e-7
+    constexpr float c[3] = {-5.000000000e-01f, 4.166579992e-02f, -1.379617257e-03f};
+    return horner(c, w);
+}
+template <typename V>
+__device__ __forceinline__ V cosm1_short(V w) {
+    constexpr float c[3] = {-4.999998510e-01f, 4.166229069e-02f, -1.368109020e-03f};
+    return horner(c, w);
+}
+template <typename V>
+__device__ __forceinline__ V cosm1_long(V w) {
+    constexpr float c[5] = {-5.000000000e-01f, 4.166664928e-02f, -1.388843870e-03f, 2.476027112e-05f,
+                            -2.600190783e-07f};
+    return horner(c, w);
+}
+// J0(z) - 1 = y r(y), y = (z/2)^2, r = -(1 - J0) / y (gen_poly.py's j0m1q, negated):
+// X = 0.25 (|z| <= 1), d = 3: |y r| error 1.4e-8, relative 8e-8;  X = 1 (|z| <= 2), d = 4:
+// 6e-8, relative 8e-8
+template <typename V>
+__device__ __forceinline__ V j0m1_tiny(V y) {   // X = 0.0625 (|z| <= 0.5), d = 2: relative 1.1e-7
+    constexpr float c[3] = {-1.000000000e+00f, 2.499962002e-01f, -2.761547454e-02f};
+    return horner(c, y);
+}
+template <typename V>
+__device__ __forceinline__ V j0m1_short(V y) {
+    constexpr float c[4] = {-1.000000000e+00f, 2.499997318e-01f, -2.777241915e-02f, 1.701718429e-03f};
+    return horner(c, y);
+}
+template <typename V>
+__device__ __forceinline__ V j0m1_long(V y) {
+    constexpr float c[5] = {-1.000000000e+00f, 2.499998212e-01f, -2.777634189e-02f, 1.732071629e-03f,
+                            -6.477852730e-05f};
+    return horner(c, y);
+}
+// J1(z) = (z/2) q((z/2)^2): X = 0.25 (|z| <= 1), d = 3, 6e-8;  X = 1 (|z| <= 2), d = 5, 6e-8
+template <typename V>
+__device__ __forceinline__ V j1q_short(V y) {
+    constexpr float c[4] = {1.000000000e+00f, -4.999986589e-01f, 8.330661058e-02f, -6.772808731e-03f};
+    return horner(c, y);
+}
+template <typename V>
+__device__ __forceinline__ V j1q_long(V y) {
+    constexpr float c[6] = {1.000000000e+00f, -5.000000000e-01f, 8.333322406e-02f, -6.943985354e-03f,
+                            3.463324101e-04f, -1.077446268e-05f};
+    return horner(c, y);
 }
 
-__device__ __forceinline__ float bessel_j0_f(float s) {
-    if (fabsf(s) <= 2.0f) return j0_series_f(s);
-    return (float)j0((double)s);
+// ---- scalar path: FP32 argument in range, FP64 argument beyond ---------------------------------
+
+// s in FP64 from the staged lattice integers p_k (c_k = 2 i_k - (m_k - 1)) and the
+// direction: s = sum_k c_k (xi_k / (2 (m_k - 1))).
+template <int NDIM>
+__device__ __forceinline__ double arg64(const float4& q, const double (&xi)[3], const double (&inv2m)[3]) {
+    double s = (double)q.x * (xi[0] * inv2m[0]);
+    s = fma((double)q.y, xi[1] * inv2m[1], s);
+    if (NDIM == 3) s = fma((double)q.z, xi[2] * inv2m[2], s);
+    return s;
 }
 
-__device__ __forceinline__ float bessel_j1_f(float s) {
-    if (fabsf(s) <= 2.0f) return j1_series_f(s);
-    return (float)j1((double)s);
+// r = s - 2 pi k in [-pi, pi] (FP64; the error of the FP64 constant 2 pi times k stays
+// below 1e-10 for |s| <= 1e6), rounded to FP32.
+__device__ __forceinline__ float reduce_2pi(double s) {
+    const double k = rint(s * 0.15915494309189535);
+    return (float)fma(-k, 6.283185307179586, s);
 }
 
-// sin and cos on the MUFU pipe for |s| <= pi (absolute error < 2^-21), accurate
-// library routine beyond.
-__device__ __forceinline__ void sincos_f(float s, float& sn, float& cs) {
-    if (fabsf(s) <= 3.14159f) {
-        sn = __sinf(s);
-        cs = __cosf(s);
+// (sin s, cos s - 1).  |z| <= 1.75: polynomials of the FP32 argument z; beyond: the FP64
+// argument reduced modulo 2 pi, and with (a, b) = (sin r/2, cos r/2) from the accurate
+// sincosf, sin s = 2 a b and cos s - 1 = -2 a^2.
+template <int NDIM>
+__device__ __forceinline__ void trig_m1(float z, const float4& q, const double (&xi)[3], const double (&inv2m)[3],
+                                        float& sn, float& cm1) {
+    if (fabsf(z) <= kTrigM32) {
+        const float w = z * z;
+        sn = z * sinc_long(w);
+        cm1 = w * cosm1_long(w);
     } else {
-        sincosf(s, &sn, &cs);
+        const float r = reduce_2pi(arg64<NDIM>(q, xi, inv2m));
+        float a, b;
+        sincosf(0.5f * r, &a, &b);
+        sn = 2.0f * a * b;
+        cm1 = -2.0f * a * a;
     }
+}
+
+// (sin s, cos s) for the adjoint's scalar path, argument as trig_m1.
+template <int NDIM>
+__device__ __forceinline__ void trig_full(float z, const float4& q, const double (&xi)[3], const double (&inv2m)[3],
+                                          float& sn, float& cs) {
+    if (fabsf(z) <= kTrigM32) {
+        const float w = z * z;
+        sn = z * sinc_long(w);
+        cs = cos_long(w);
+    } else {
+        sincosf(reduce_2pi(arg64<NDIM>(q, xi, inv2m)), &sn, &cs);
+    }
+}
+
+// J0(s) - 1: -y q(y) with y = (z/2)^2 for |z| <= 2; beyond, FP64 j0 of the FP64 argument.
+template <int NDIM>
+__device__ __forceinline__ float j0m1_scalar(float z, const float4& q, const double (&xi)[3],
+                                             const double (&inv2m)[3]) {
+    if (fabsf(z) <= kBesselM32) {
+        const float y = 0.25f * z * z;
+        return y * j0m1_long(y);
+    }
+    return (float)(j0(arg64<NDIM>(q, xi, inv2m)) - 1.0);
+}
+
+// J1(s): (z/2) q((z/2)^2) for |z| <= 2; beyond, FP64 j1 of the FP64 argument.
+template <int NDIM>
+__device__ __forceinline__ float j1_scalar(float z, const float4& q, const double (&xi)[3],
+                                           const double (&inv2m)[3]) {
+    if (fabsf(z) <= kBesselM32) {
+        const float h = 0.5f * z;
+        return h * j1q_long(h * h);
+    }
+    return (float)j1(arg64<NDIM>(q, xi, inv2m));
 }
 
 // Per-lane direction coefficients.
@@ -185,13 +321,14 @@ __device__ __forceinline__ void ht_dir(const EvalPlan& P, const HtItem& it, int 
     hd.valid = r < it.nd;
     hd.d = hd.valid ? P.perm[(long long)it.set * P.D + P.boff[(long long)it.set * (NO + 1) + it.o] + r] : 0;
     const double* xp = P.dirs + ((long long)it.set * P.D + hd.d) * NDIM;
+    // 2 log2(e) for Laplace (|xi_k| / (m_k - 1) log2 e), 1 otherwise (xi_k / (2 (m_k - 1)))
+    const double f = KERNEL == TOPOT_LAPLACE ? 2.8853900817779268 : 1.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         hd.xi[k] = k < NDIM ? xp[k] : 0.0;
-        const double mk = (double)(it.I->m[k] - 1);
         if (k >= NDIM) hd.w[k] = 0.0f;
-        else if (KERNEL == TOPOT_LAPLACE) hd.w[k] = (float)(fabs(hd.xi[k]) / mk * 1.4426950408889634);
-        else hd.w[k] = (float)(hd.xi[k] / (2.0 * mk));
+        else if (KERNEL == TOPOT_LAPLACE) hd.w[k] = (float)(fabs(hd.xi[k]) * (f * it.I->inv2m[k]));
+        else hd.w[k] = (float)(hd.xi[k] * it.I->inv2m[k]);
     }
 }
 
@@ -208,65 +345,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Short polynomial kernels: degree-d Chebyshev interpolants on [0, X] written in the
-// power basis (constants derived by gen_poly.py from the functions' own series; the
-// listed bounds are the worst absolute errors of the FP32 Horner evaluation).
-//   cos(sqrt w): X = 0.5625 (|z| <= 0.75), d = 3, 8e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
-//   J0(2 sqrt y): X = 0.25 (|z| <= 1), d = 3, 9e-8;       X = 1 (|z| <= 2), d = 5, 5e-8
-template <int N>
-__device__ __forceinline__ float2 horner2(const float (&c)[N], float2 x) {
-    float2 p = make_float2(c[N - 1], c[N - 1]);
-#pragma unroll
-    for (int k = N - 2; k >= 0; --k) p = fma2(p, x, make_float2(c[k], c[k]));
-    return p;
-}
-
-__device__ __forceinline__ float2 cos_short2(float2 w) {
-    constexpr float c[4] = {1.000000000e+00f, -4.999988973e-01f, 4.165696725e-02f, -1.361225732e-03f};
-    return horner2(c, w);
-}
-
-__device__ __forceinline__ float2 cos_long2(float2 w) {
-    constexpr float c[6] = {1.000000000e+00f, -4.999999702e-01f, 4.166659340e-02f, -1.388788689e-03f,
-                            2.473820496e-05f, -2.569863113e-07f};
-    return horner2(c, w);
-}
-
-// sin z = z q(z^2): X = 0.5625 (|z| <= 0.75), d = 3, 4e-8;  X = 3.0625 (|z| <= 1.75), d = 5, 7e-8
-__device__ __forceinline__ float2 sinc_short2(float2 w) {
-    constexpr float c[4] = {1.000000000e+00f, -1.666665524e-01f, 8.332253434e-03f, -1.953341998e-04f};
-    return horner2(c, w);
-}
-
-__device__ __forceinline__ float2 sinc_long2(float2 w) {
-    constexpr float c[6] = {1.000000000e+00f, -1.666666716e-01f, 8.333328180e-03f, -1.984049450e-04f,
-                            2.750829026e-06f, -2.361634976e-08f};
-    return horner2(c, w);
-}
-
-__device__ __forceinline__ float2 j0_short2(float2 y) {
-    constexpr float c[4] = {9.999999404e-01f, -9.999933243e-01f, 2.498667836e-01f, -2.692156099e-02f};
-    return horner2(c, y);
-}
-
-// J1(z) = (z/2) q((z/2)^2): X = 0.25 (|z| <= 1), d = 3, 6e-8;  X = 1 (|z| <= 2), d = 5, 6e-8
-__device__ __forceinline__ float2 j1q_short2(float2 y) {
-    constexpr float c[4] = {1.000000000e+00f, -4.999986589e-01f, 8.330661058e-02f, -6.772808731e-03f};
-    return horner2(c, y);
-}
-
-__device__ __forceinline__ float2 j1q_long2(float2 y) {
-    constexpr float c[6] = {1.000000000e+00f, -5.000000000e-01f, 8.333322406e-02f, -6.943985354e-03f,
-                            3.463324101e-04f, -1.077446268e-05f};
-    return horner2(c, y);
-}
-
-__device__ __forceinline__ float2 j0_long2(float2 y) {
-    constexpr float c[6] = {1.000000000e+00f, -9.999999404e-01f, 2.499992549e-01f, -2.777458727e-02f,
-                            1.729921903e-03f, -6.387370377e-05f};
-    return horner2(c, y);
-}
-
 // Compensated add of a block sum x into (s, nc) for two sums at once.
 __device__ __forceinline__ void kahan2_add(float2& s, float2& nc, float2 x) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
@@ -277,9 +355,12 @@ __device__ __forceinline__ void kahan2_add(float2& s, float2& nc, float2 x) {
     s = t;
 }
 
-// Fourier: odd pairs take sin and cos from the MUFU pipe, even pairs evaluate both as
-// polynomials in w = z^2 on the FMA pipe; half and half keeps both pipes busy (a MUFU
-// sin/cos costs two XU cycles, the polynomial pair about 9 FP32 operations).
+// kbar(s) - kbar(0) for a direction pair.  Fourier: odd pairs take sin and cos from the
+// MUFU pipe, even pairs evaluate sin and cos - 1 as polynomials in w = z^2 on the FMA
+// pipe; half and half keeps both pipes busy (a MUFU sin/cos costs two XU cycles, the
+// polynomial pair about 9 FP32 operations).  The MUFU pairs return cos s itself: their
+// constant is removed once per round (the warp's sum of the staged values, see
+// ht_packed_range), since MUFU's absolute error would not shrink with cos s - 1 anyway.
 template <int KERNEL, int PATH>
 __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_cos) {
     if (KERNEL == TOPOT_LAPLACE) {
@@ -290,19 +371,19 @@ __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_
             k[1] = make_float2(__cosf(z.x), __cosf(z.y));
         } else {
             const float2 w = mul2(z, z);
-            k[0] = mul2(z, PATH == 2 ? sinc_short2(w) : sinc_long2(w));
-            k[1] = PATH == 2 ? cos_short2(w) : cos_long2(w);
+            k[0] = mul2(z, PATH == 3 ? sinc_tiny(w) : (PATH == 2 ? sinc_short(w) : sinc_long(w)));
+            k[1] = mul2(w, PATH == 3 ? cosm1_tiny(w) : (PATH == 2 ? cosm1_short(w) : cosm1_long(w)));
         }
-    } else if (KERNEL == TOPOT_SINE) {   // cos s; the sign of kbar = -cos is applied at the combine
+    } else if (KERNEL == TOPOT_SINE) {   // cos s - 1; the sign of kbar = -cos is applied at the combine
         if (mufu_cos) {
             k[0] = make_float2(__cosf(z.x), __cosf(z.y));
         } else {
             const float2 w = mul2(z, z);
-            k[0] = PATH == 2 ? cos_short2(w) : cos_long2(w);
+            k[0] = mul2(w, PATH == 3 ? cosm1_tiny(w) : (PATH == 2 ? cosm1_short(w) : cosm1_long(w)));
         }
-    } else {
-        const float2 y = mul2(z, z);   // z is already halved
-        k[0] = PATH == 2 ? j0_short2(y) : j0_long2(y);
+    } else {   // J0 - 1; z is already halved
+        const float2 y = mul2(z, z);
+        k[0] = mul2(y, PATH == 3 ? j0m1_tiny(y) : (PATH == 2 ? j0m1_short(y) : j0m1_long(y)));
     }
 }
 
@@ -358,12 +439,74 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
     }
 }
 
-template <int NDIM, int KERNEL, int DL, typename Tval>
+// Sum of the table values of staged points [e0 + i0, e0 + i1) (one warp's slice of a
+// round), exact in 64-bit integers; every lane gets it.
+template <typename Tval>
+__device__ __forceinline__ long long warp_value_sum(const TablesDev& t, const HtItem& it, long long e0, int i0,
+                                                    int i1, int lane) {
+    const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
+    long long v = 0;
+    for (int i = i0 + lane; i < i1; i += 32) v += aval[it.base + e0 + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Laplace exponent in FP64 for the scalar path: (s - M) log2 e = sum_k q_k |xi_k| / (m_k - 1)
+// log2 e from the staged integers q_k <= 0.
+template <int NDIM>
+__device__ __forceinline__ double lap_arg64(const float4& q, const double (&xi)[3], const double (&invm)[3]) {
+    constexpr double kLog2e = 1.4426950408889634;
+    double s = (double)q.x * (fabs(xi[0]) * invm[0]);
+    s = fma((double)q.y, fabs(xi[1]) * invm[1], s);
+    if (NDIM == 3) s = fma((double)q.z, fabs(xi[2]) * invm[2], s);
+    return s * kLog2e;
+}
+
+// Which items a forward or adjoint FP32C launch takes.  With one direction per lane
+// (kRoleAll) every item runs on the scalar path.  With two or more, a tile whose
+// directions all lie in the FP32 argument range runs on the packed path (kRolePacked)
+// and any other tile on the scalar path (kRoleWide): two launches of one item list, each
+// skipping the other's tiles, so that the FP64 code of the wide tiles does not weigh on
+// the registers of the packed kernel.  Both decide from the same tile maximum of M.
+enum HtRole : int { kRoleAll = 0, kRolePacked = 1, kRoleWide = 2 };
+
+// Largest M = sum_k |xi_k| / 2 (a bound on |<xi, v>|) over the tile's directions; every
+// lane of the warp gets it.
+template <int NDIM, int DL>
+__device__ __forceinline__ float tile_mloc(const EvalPlan& P, const HtItem& it, int tile, int lane) {
+    constexpr int NO = 1 << NDIM;
+    float m = 0.0f;
+#pragma unroll
+    for (int j = 0; j < DL; ++j) {
+        const int r = tile * 32 * DL + j * 32 + lane;
+        if (r < it.nd) {
+            const int d = P.perm[(long long)it.set * P.D + P.boff[(long long)it.set * (NO + 1) + it.o] + r];
+            const double* xp = P.dirs + ((long long)it.set * P.D + d) * NDIM;
+            double a = 0.0;
+#pragma unroll
+            for (int k = 0; k < NDIM; ++k) a += fabs(xp[k]);
+            m = fmaxf(m, (float)(0.5 * a));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
+template <int NDIM, int KERNEL>
+__device__ __forceinline__ float packed_limit() {
+    return KERNEL == TOPOT_LAPLACE ? kLaplaceM32 : (KERNEL == TOPOT_BESSEL ? kBesselM32 : kTrigM32);
+}
+
+template <int NDIM, int KERNEL, int DL, typename Tval, int ROLE>
 __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, double* part) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr int TDH = 32 * DL;
     constexpr int NO = 1 << NDIM;
     constexpr int NPR = DL / 2;                 // direction pairs per lane (packed path)
+    constexpr bool SPLIT = KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE;
+    constexpr int CCOS = KERNEL == TOPOT_FOURIER ? 1 : 0;   // component holding cos s - 1
     // staging buffer: scalar path (p0, p1, p2, value) per point; packed path
     // (p0, p0, p1, p1), (p2, p2, v, v); reused for the per-item reduction
     __shared__ __align__(16) float4 A[2 * kHtSub];
@@ -372,51 +515,78 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
     __shared__ long long sh_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long nitems = P.ctl[2];
+    int* counter = ROLE == kRoleWide ? &P.ctl[3] : &P.ctl[0];
 
     while (true) {
         __syncthreads();
-        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        if (tid == 0) sh_item = atomicAdd(counter, 1);
         __syncthreads();
         const long long item = sh_item;
         if (item >= nitems) break;
         int tile;
         const HtItem it = ht_item(P, t, item, NO, TDH, tile);
-        HtDir hd[DL];
-        float mloc = 0.0f;   // max over this lane's directions of sum |xi_k| / 2 >= |<xi, v>|
-#pragma unroll
-        for (int j = 0; j < DL; ++j) {
-            ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
-            if (hd[j].valid)
-                mloc = fmaxf(mloc, (float)(0.5 * (fabs(hd[j].xi[0]) + fabs(hd[j].xi[1]) + fabs(hd[j].xi[2]))));
-        }
         // tile-uniform choice of the evaluation path (all warps see the same tile)
+        const float mloc = tile_mloc<NDIM, DL>(P, it, tile, lane);
+        const bool in_range = mloc <= packed_limit<NDIM, KERNEL>();
+        // an item of the other launch: no points and no partial written (a skip that keeps
+        // the loop's shape, which the packed path's register allocation prefers)
+        const bool mine = !((ROLE == kRolePacked && !in_range) || (ROLE == kRoleWide && in_range));
+        if (ROLE == kRoleWide && !mine) continue;   // the wide launch skips at once
+        const long long e_end = mine ? it.e_end : it.e_begin;
+        HtDir hd[DL];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-        // 0: scalar generic path; packed paths by the range of |<xi, v>| <= mloc:
-        //   Fourier, sine: 2 (<= 0.75, short cos), 1 (<= 1.75, long cos)
-        //   Bessel:  2 (<= 1, short J0), 1 (<= 2, long J0)
+        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+        // 0: scalar path; packed paths by the range of |<xi, v>| <= mloc:
+        //   Laplace: 1 (<= 1)
+        //   Fourier, sine: 3 (<= 0.5, tiny), 2 (<= 0.75, short), 1 (<= 1.75, long polynomials)
+        //   Bessel:  3 (<= 0.5, tiny), 2 (<= 1, short), 1 (<= 2, long)
+        // (directions are sorted by M within their orthant, so most tiles are narrow)
         int path = 0;
-        if (NPR > 0) {
-            if (KERNEL == TOPOT_LAPLACE) path = 1;
-            else if (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE)
-                path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
-            else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
-        }
+        if (ROLE == kRolePacked)
+            path = (KERNEL == TOPOT_LAPLACE) ? 1
+                 : (mloc <= 0.5f ? 3 : (mloc <= (KERNEL == TOPOT_BESSEL ? 1.0f : 0.75f) ? 2 : 1));
 
         float acc[DL][NC], cmp[DL][NC];
+        double off[DL][NC];   // FP64 part of each sum (rescaled Laplace rounds, MUFU constants)
 #pragma unroll
         for (int j = 0; j < DL; ++j)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
+            for (int c = 0; c < NC; ++c) {
+                acc[j][c] = cmp[j][c] = 0.0f;
+                off[j][c] = 0.0;
+            }
 
-        if (path == 0) {
-            for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
-                const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
+        if constexpr (ROLE != kRolePacked) {
+            // Laplace with large M: FP64 exponents, each round of staged points scaled by
+            // its own largest term (no underflow, error independent of M)
+            const bool rescale = KERNEL == TOPOT_LAPLACE && mloc > kLaplaceM32;
+            double inv[3];   // Laplace: 1 / (m_k - 1); others: 1 / (2 (m_k - 1))
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                inv[k] = k < NDIM ? (KERNEL == TOPOT_LAPLACE ? 2.0 : 1.0) * it.I->inv2m[k] : 0.0;
+            for (long long e0 = it.e_begin; e0 < e_end; e0 += kHtSub) {
+                const int cnt = (int)min((long long)kHtSub, e_end - e0);
                 __syncthreads();
                 ht_stage<NDIM, KERNEL, false, Tval>(t, it, e0, cnt, A, nullptr);
                 __syncthreads();
                 const int per = (cnt + kHtWarps - 1) / kHtWarps;
                 const int ws = warp * per, we = min(cnt, ws + per);
+                if (KERNEL == TOPOT_LAPLACE && rescale) {
+                    if (ws < we) {
+#pragma unroll
+                        for (int j = 0; j < DL; ++j) {
+                            double zr = -1e300;
+                            for (int e = ws; e < we; ++e) zr = fmax(zr, lap_arg64<NDIM>(A[e], hd[j].xi, inv));
+                            float sr = 0.0f, cr = 0.0f;
+                            for (int e = ws; e < we; ++e) {
+                                const float4 q = A[e];
+                                kahan_add(sr, cr, q.w * exp2f((float)(lap_arg64<NDIM>(q, hd[j].xi, inv) - zr)));
+                            }
+                            off[j][0] += ((double)sr - (double)cr) * exp2(zr);
+                        }
+                    }
+                    continue;
+                }
                 for (int e = ws; e < we; ++e) {
                     const float4 q = A[e];
 #pragma unroll
@@ -427,16 +597,16 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
                         if (KERNEL == TOPOT_LAPLACE) {
                             kahan_add(acc[j][0], cmp[j][0], q.w * exp2f(z));
                         } else if (KERNEL == TOPOT_FOURIER) {
-                            float sn, cs;
-                            sincos_f(z, sn, cs);
+                            float sn, cm;
+                            trig_m1<NDIM>(z, q, hd[j].xi, inv, sn, cm);
                             kahan_add(acc[j][0], cmp[j][0], q.w * sn);
-                            kahan_add(acc[j][1], cmp[j][1], q.w * cs);
+                            kahan_add(acc[j][1], cmp[j][1], q.w * cm);
                         } else if (KERNEL == TOPOT_SINE) {
-                            float sn, cs;
-                            sincos_f(z, sn, cs);
-                            kahan_add(acc[j][0], cmp[j][0], q.w * cs);
+                            float sn, cm;
+                            trig_m1<NDIM>(z, q, hd[j].xi, inv, sn, cm);
+                            kahan_add(acc[j][0], cmp[j][0], q.w * cm);
                         } else {
-                            kahan_add(acc[j][0], cmp[j][0], q.w * bessel_j0_f(z));
+                            kahan_add(acc[j][0], cmp[j][0], q.w * j0m1_scalar<NDIM>(z, q, hd[j].xi, inv));
                         }
                     }
                 }
@@ -446,6 +616,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
 #pragma unroll
                 for (int c = 0; c < NC; ++c) cmp[j][c] = -cmp[j][c];   // report as s + nc
         } else if constexpr (NPR > 0) {
+            (void)in_range;
             // packed coefficients: pair p covers directions 2p and 2p + 1 of this lane;
             // Bessel uses z / 2 so that y = (z / 2)^2 is one multiply
             float2 w[NPR][3];
@@ -459,9 +630,10 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             for (int pq = 0; pq < NPR; ++pq)
 #pragma unroll
                 for (int c = 0; c < NC; ++c) s2[pq][c] = n2[pq][c] = make_float2(0.0f, 0.0f);
+            long long vsum = 0;   // this warp's staged values: the constant of the MUFU pairs' cos
 
-            for (long long e0 = it.e_begin; e0 < it.e_end; e0 += kHtSub) {
-                const int cnt = (int)min((long long)kHtSub, it.e_end - e0);
+            for (long long e0 = it.e_begin; e0 < e_end; e0 += kHtSub) {
+                const int cnt = (int)min((long long)kHtSub, e_end - e0);
                 __syncthreads();
                 // pad the round to 8 points per warp per block with zero-value points
                 const int cnt_pad = (cnt + kHtWarps * 8 - 1) / (kHtWarps * 8) * (kHtWarps * 8);
@@ -469,7 +641,9 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
                 __syncthreads();
                 const int per = cnt_pad / kHtWarps;
                 const int ws = warp * per, we = ws + per;
-                if (path == 2) ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2);
+                if (SPLIT && NPR > 1) vsum += warp_value_sum<Tval>(t, it, e0, ws, min(we, cnt), lane);
+                if (KERNEL != TOPOT_LAPLACE && path == 3) ht_packed_range<NDIM, KERNEL, NPR, 3>(A, ws, we, w, s2, n2);
+                else if (KERNEL != TOPOT_LAPLACE && path == 2) ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2);
                 else ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2);
             }
 #pragma unroll
@@ -480,6 +654,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
                     cmp[2 * pq][c] = n2[pq][c].x;
                     acc[2 * pq + 1][c] = s2[pq][c].y;
                     cmp[2 * pq + 1][c] = n2[pq][c].y;
+                    if (SPLIT && (pq & 1) && c == CCOS) off[2 * pq][c] = off[2 * pq + 1][c] = -(double)vsum;
                 }
         }
         // fixed-order FP64 reduction over warps -> item partial (red aliases the stage)
@@ -488,9 +663,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
         for (int j = 0; j < DL; ++j)
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] + (double)cmp[j][c];
+            {
+                double r = (double)acc[j][c] + (double)cmp[j][c];
+                if constexpr (ROLE != kRolePacked || SPLIT) r += off[j][c];
+                red[warp][(j * 32 + lane) * NC + c] = r;
+            }
         __syncthreads();
-        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+        for (int i = tid; mine && i < TDH * NC; i += kHtBlock) {
             double s = 0.0;
 #pragma unroll
             for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
@@ -574,6 +753,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev
     const float Kf = (float)K;
     const float inv_h = (float)(1.0 / P.ktab_h);
     const float v0 = (float)((0.5 - P.ktab_a / P.ktab_h) / (double)K);
+    const double inv_hk = 1.0 / (P.ktab_h * (double)K);
 
     while (true) {
         __syncthreads();
@@ -589,10 +769,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_table_f32(EvalPlan P, TablesDev
             HtDir hd;
             ht_dir<NDIM, TOPOT_TABLE>(P, it, tile * TDH + j * 32 + lane, hd);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const double scale = 2.0 * (double)(it.I->m[k] - 1) * P.ktab_h * (double)K;
-                wt[j][k] = k < NDIM ? (float)(hd.xi[k] / scale) : 0.0f;
-            }
+            for (int k = 0; k < 3; ++k) wt[j][k] = k < NDIM ? (float)(hd.xi[k] * (it.I->inv2m[k] * inv_hk)) : 0.0f;
         }
         float acc[DL][NC], cmp[DL][NC];
 #pragma unroll
@@ -793,8 +970,8 @@ __device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int
                         cs = make_float2(__cosf(z.x), __cosf(z.y));
                     } else {
                         const float2 ww = mul2(z, z);
-                        sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
-                        cs = PATH == 2 ? cos_short2(ww) : cos_long2(ww);
+                        sn = mul2(z, PATH == 2 ? sinc_short(ww) : sinc_long(ww));
+                        cs = PATH == 2 ? cos_short(ww) : cos_long(ww);
                     }
                     t[0] = mul2(v2, cs);
                     t[1] = mul2(v2, sn);
@@ -804,12 +981,12 @@ __device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int
                         sn = make_float2(__sinf(z.x), __sinf(z.y));
                     } else {
                         const float2 ww = mul2(z, z);
-                        sn = mul2(z, PATH == 2 ? sinc_short2(ww) : sinc_long2(ww));
+                        sn = mul2(z, PATH == 2 ? sinc_short(ww) : sinc_long(ww));
                     }
                     t[0] = mul2(v2, sn);
                 } else {   // z is halved: kappa = -J1(2 z) = -z q(z^2)
                     const float2 y = mul2(z, z);
-                    const float2 j1 = mul2(z, PATH == 2 ? j1q_short2(y) : j1q_long2(y));
+                    const float2 j1 = mul2(z, PATH == 2 ? j1q_short(y) : j1q_long(y));
                     t[0] = mul2(make_float2(-v2.x, -v2.y), j1);
                 }
 #pragma unroll
@@ -827,7 +1004,7 @@ __device__ __forceinline__ void ht_adj_packed_range(const float4* A, int ws, int
     }
 }
 
-template <int NDIM, int KERNEL, int DL, typename Tval>
+template <int NDIM, int KERNEL, int DL, typename Tval, int ROLE>
 __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t, double* part) {
     constexpr int NK = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr int NC = NK * NDIM;
@@ -842,15 +1019,23 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
     __shared__ long long sh_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long nitems = P.ctl[2];
+    int* counter = ROLE == kRoleWide ? &P.ctl[3] : &P.ctl[0];
 
     while (true) {
         __syncthreads();
-        if (tid == 0) sh_item = atomicAdd(&P.ctl[0], 1);
+        if (tid == 0) sh_item = atomicAdd(counter, 1);
         __syncthreads();
         const long long item = sh_item;
         if (item >= nitems) break;
         int tile;
         const HtItem it = ht_item(P, t, item, NO, TDH, tile);
+        const float mloc = tile_mloc<NDIM, DL>(P, it, tile, lane);
+        const bool in_range = mloc <= packed_limit<NDIM, KERNEL>();
+        // an item of the other launch: no points and no partial written (a skip that keeps
+        // the loop's shape, which the packed path's register allocation prefers)
+        const bool mine = !((ROLE == kRolePacked && !in_range) || (ROLE == kRoleWide && in_range));
+        if (ROLE == kRoleWide && !mine) continue;   // the wide launch skips at once
+        const long long e_end = mine ? it.e_end : it.e_begin;
         HtDir hd[DL];
 #pragma unroll
         for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
@@ -860,23 +1045,17 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[j][c] = cmp[j][c] = 0.0f;
 
-        float mloc = 0.0f;
+        // packed paths: as the forward, DL / 2 direction pairs per lane
+        int path = 0;
+        if (ROLE == kRolePacked) path = (KERNEL == TOPOT_LAPLACE) ? 1 : (mloc <= (KERNEL == TOPOT_BESSEL ? 1.0f : 0.75f) ? 2 : 1);
+        double off[DL][NC];   // FP64 part of each sum (rescaled Laplace rounds)
 #pragma unroll
         for (int j = 0; j < DL; ++j)
-            if (hd[j].valid)
-                mloc = fmaxf(mloc, (float)(0.5 * (fabs(hd[j].xi[0]) + fabs(hd[j].xi[1]) + fabs(hd[j].xi[2]))));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mloc = fmaxf(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-        int path = 0;   // packed paths: as the forward, DL / 2 direction pairs per lane
-        if (DL >= 2) {
-            if (KERNEL == TOPOT_LAPLACE) path = 1;
-            else if (KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE)
-                path = mloc <= 0.75f ? 2 : (mloc <= 1.75f ? 1 : 0);
-            else path = mloc <= 1.0f ? 2 : (mloc <= 2.0f ? 1 : 0);
-        }
-        if constexpr (DL >= 2) {
+            for (int c = 0; c < NC; ++c) off[j][c] = 0.0;
+        if constexpr (ROLE == kRolePacked) {
             constexpr int NPR = DL / 2;
-            if (path != 0) {
+            {
                 const float wsc = KERNEL == TOPOT_BESSEL ? 0.5f : 1.0f;
                 float2 w[NPR][3], xa[3], xb[3];
 #pragma unroll
@@ -899,8 +1078,8 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                 for (int r = 0; r < NPR; ++r)
 #pragma unroll
                     for (int c = 0; c < NC; ++c) s2[r][c] = n2[r][c] = make_float2(0.0f, 0.0f);
-                for (long long e0 = it.e_begin; e0 < it.e_end; e0 += SUB) {
-                    const int cnt = (int)min((long long)SUB, it.e_end - e0);
+                for (long long e0 = it.e_begin; e0 < e_end; e0 += SUB) {
+                    const int cnt = (int)min((long long)SUB, e_end - e0);
                     __syncthreads();
                     const int cnt_pad = (cnt + kHtWarps * 8 - 1) / (kHtWarps * 8) * (kHtWarps * 8);
                     ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr, cnt_pad);
@@ -921,13 +1100,43 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                     }
             }
         }
-        for (long long e0 = it.e_begin; path == 0 && e0 < it.e_end; e0 += SUB) {
-            const int cnt = (int)min((long long)SUB, it.e_end - e0);
+        const bool rescale = KERNEL == TOPOT_LAPLACE && mloc > kLaplaceM32;
+        double inv[3];   // Laplace: 1 / (m_k - 1); others: 1 / (2 (m_k - 1))
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            inv[k] = k < NDIM ? (KERNEL == TOPOT_LAPLACE ? 2.0 : 1.0) * it.I->inv2m[k] : 0.0;
+        for (long long e0 = it.e_begin; ROLE != kRolePacked && e0 < e_end; e0 += SUB) {
+            const int cnt = (int)min((long long)SUB, e_end - e0);
             __syncthreads();
             ht_stage<NDIM, KERNEL, true, Tval>(t, it, e0, cnt, A, X);
             __syncthreads();
             const int per = (cnt + kHtWarps - 1) / kHtWarps;
             const int ws = warp * per, we = min(cnt, ws + per);
+            if (KERNEL == TOPOT_LAPLACE && rescale) {
+                // FP64 exponents; each round scaled by its own largest term (as the forward)
+                if (ws < we) {
+#pragma unroll
+                    for (int j = 0; j < DL; ++j) {
+                        double zr = -1e300;
+                        for (int e = ws; e < we; ++e) zr = fmax(zr, lap_arg64<NDIM>(A[e], hd[j].xi, inv));
+                        float sr[NC], cr[NC];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) sr[c] = cr[c] = 0.0f;
+                        for (int e = ws; e < we; ++e) {
+                            const float4 q = A[e];
+                            const float4 x = X[e];
+                            const float xs[3] = {x.x, x.y, x.z};
+                            const float tk = q.w * exp2f((float)(lap_arg64<NDIM>(q, hd[j].xi, inv) - zr));
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) kahan_add(sr[c], cr[c], tk * xs[c]);
+                        }
+                        const double sc = exp2(zr);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) off[j][c] += ((double)sr[c] - (double)cr[c]) * sc;
+                    }
+                }
+                continue;
+            }
             for (int e = ws; e < we; ++e) {
                 const float4 q = A[e];
                 const float4 x = X[e];
@@ -939,7 +1148,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                     if (NDIM == 3) z = fmaf(q.z, hd[j].w[2], z);
                     if (KERNEL == TOPOT_FOURIER) {
                         float sn, cs;
-                        sincos_f(z, sn, cs);
+                        trig_full<NDIM>(z, q, hd[j].xi, inv, sn, cs);
                         const float tc = q.w * cs, ts = q.w * sn;
 #pragma unroll
                         for (int k = 0; k < NDIM; ++k) {
@@ -952,9 +1161,9 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                             kv = exp2f(z);
                         } else if (KERNEL == TOPOT_SINE) {   // kappa = sin
                             float cs;
-                            sincos_f(z, kv, cs);
+                            trig_full<NDIM>(z, q, hd[j].xi, inv, kv, cs);
                         } else {
-                            kv = -bessel_j1_f(z);
+                            kv = -j1_scalar<NDIM>(z, q, hd[j].xi, inv);
                         }
                         const float tk = q.w * kv;
 #pragma unroll
@@ -967,9 +1176,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
         for (int j = 0; j < DL; ++j)
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                red[warp][(j * 32 + lane) * NC + c] = (double)acc[j][c] - (double)cmp[j][c];
+            {
+                double r = (double)acc[j][c] - (double)cmp[j][c];
+                if constexpr (ROLE != kRolePacked) r += off[j][c];
+                red[warp][(j * 32 + lane) * NC + c] = r;
+            }
         __syncthreads();
-        for (int i = tid; i < TDH * NC; i += kHtBlock) {
+        for (int i = tid; mine && i < TDH * NC; i += kHtBlock) {
             double s = 0.0;
 #pragma unroll
             for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
@@ -1098,11 +1311,13 @@ __global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision
     double v[2];
     gather_partials(P, NO, tdh, nc, b, d, o, part, v);
     const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
-    double scale = kernel == TOPOT_SINE ? -sign : sign;   // sine: the partials hold sum v cos s
+    // sine: the partials hold sum v (cos s - 1), kbar = -cos
+    double scale = kernel == TOPOT_SINE ? -sign : sign;
     if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
         double M = 0.0;
         for (int k = 0; k < n; ++k) M += fabs(xi[k]);
-        scale *= exp(0.5 * M);
+        M *= 0.5;
+        scale = M <= kLaplaceMaxM ? scale * exp(M) : __longlong_as_double(0x7ff8000000000000ll);
     }
     for (int c = 0; c < nc; ++c) out[gid * nc + c] = v[c] * scale;
 }
@@ -1124,7 +1339,8 @@ __global__ void k_ht_adj_combine(EvalPlan P, int n, int B, int kernel, int preci
     if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
         double M = 0.0;
         for (int k = 0; k < n; ++k) M += fabs(xi[k]);
-        scale *= exp(0.5 * M);
+        M *= 0.5;
+        scale = M <= kLaplaceMaxM ? scale * exp(M) : __longlong_as_double(0x7ff8000000000000ll);
     }
     double g[3] = {0.0, 0.0, 0.0};
     const int b0 = P.nsets == 1 ? 0 : set, b1 = P.nsets == 1 ? B : set + 1;
@@ -1152,25 +1368,40 @@ static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precis
         else k_ht_f64<NDIM, KERNEL, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
         return cudaGetLastError();
     }
+    // two or more directions per lane: the packed launch, then the launch that takes the
+    // tiles outside the packed range (it only skips items when there are none)
+    const int wide_grid = std::max(1, grid / 4);
     if (adjoint) {
         switch (dl) {
-            case 1: k_ht_adj_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
-            case 2: k_ht_adj_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 1: k_ht_adj_f32<NDIM, KERNEL, 1, Tval, kRoleAll><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 2:
+                k_ht_adj_f32<NDIM, KERNEL, 2, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_adj_f32<NDIM, KERNEL, 2, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                break;
             case 4:
                 if (KERNEL == TOPOT_FOURIER) return cudaErrorInvalidValue;
-                k_ht_adj_f32<NDIM, (KERNEL == TOPOT_FOURIER ? TOPOT_LAPLACE : KERNEL), 4, Tval>
+                k_ht_adj_f32<NDIM, (KERNEL == TOPOT_FOURIER ? TOPOT_LAPLACE : KERNEL), 4, Tval, kRolePacked>
                     <<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_adj_f32<NDIM, (KERNEL == TOPOT_FOURIER ? TOPOT_LAPLACE : KERNEL), 4, Tval, kRoleWide>
+                    <<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
                 break;
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (dl) {
-            case 1: k_ht_f32<NDIM, KERNEL, 1, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
-            case 2: k_ht_f32<NDIM, KERNEL, 2, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
-            case 4: k_ht_f32<NDIM, KERNEL, 4, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 1: k_ht_f32<NDIM, KERNEL, 1, Tval, kRoleAll><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 2:
+                k_ht_f32<NDIM, KERNEL, 2, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_f32<NDIM, KERNEL, 2, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                break;
+            case 4:
+                k_ht_f32<NDIM, KERNEL, 4, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_f32<NDIM, KERNEL, 4, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                break;
             case 8:
                 if (KERNEL != TOPOT_LAPLACE) return cudaErrorInvalidValue;
-                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
+                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
                 break;
             default: return cudaErrorInvalidValue;
         }

@@ -69,6 +69,9 @@ struct ImgDesc {
     FastDiv div_spr;        // division by spr
     FastDiv div_segs;       // division by segs_per_row
     FastDiv div_tpp;        // division by tiles_per_plane
+    // evaluation kernels: 1 / (2 (m_k - 1)) in FP64 (0 for an axis of length 1), so that
+    // per-direction weights take a multiply rather than an FP64 division
+    double inv2m[kMaxDim];
 };
 
 // Device view of a tables handle.

@@ -63,7 +63,85 @@ __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
     }
 }
 
+// Hybrid transforms: the directions of an orthant are also ordered by M = sum_k |xi_k|
+// (ties by direction id), so that a tile of 32 DL consecutive directions spans a narrow
+// range of |<xi, v>| and its polynomial degree (chosen per tile from the largest M) stays
+// low.  One block per direction set sorts the keys
+//   orthant (3 bits) | FP32 bits of M (order-preserving for M >= 0) | direction id (29 bits)
+// with a bitonic network in shared memory; sets of more than kSortDirsMax directions keep
+// the plain orthant grouping.
+constexpr int kSortDirsMax = 8192;
+
+__global__ void __launch_bounds__(1024) k_dir_sort(EvalPlan P, int n) {
+    extern __shared__ unsigned long long key[];
+    __shared__ int cnt[8];
+    const int set = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int NO = 1 << n;
+    const double* dirs = P.dirs + (long long)set * P.D * n;
+    int L = 1;
+    while (L < P.D) L <<= 1;
+    if (tid < 8) cnt[tid] = 0;
+    __syncthreads();
+    for (int d = tid; d < L; d += 1024) {
+        unsigned long long k = ~0ull;   // padding sorts last
+        if (d < P.D) {
+            const double* xi = dirs + (long long)d * n;
+            double m = 0.0;
+            for (int c = 0; c < n; ++c) m += fabs(xi[c]);
+            const int o = orthant_of(xi, n);
+            atomicAdd(&cnt[o], 1);
+            k = ((unsigned long long)o << 61) | ((unsigned long long)__float_as_uint((float)m) << 29) |
+                (unsigned long long)d;
+        }
+        key[d] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= L; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < L / 2; i += 1024) {
+                const int lo = 2 * i - (i & (stride - 1));   // pairs (lo, lo + stride)
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    int* bo = P.boff + (long long)set * (NO + 1);
+    if (tid == 0) {
+        int run = 0;
+        for (int o = 0; o < NO; ++o) {
+            bo[o] = run;
+            run += cnt[o];
+        }
+        bo[NO] = run;
+    }
+    __syncthreads();
+    int* perm = P.perm + (long long)set * P.D;
+    for (int i = tid; i < P.D; i += 1024) {
+        const unsigned long long k = key[i];
+        const int d = (int)(k & ((1ull << 29) - 1));
+        const int o = (int)(k >> 61);
+        perm[i] = d;
+        P.rank[(long long)set * P.D + d] = i - bo[o];
+    }
+}
+
 cudaError_t launch_dir_prep(const EvalPlan& P, int n, cudaStream_t st) {
+    if (P.mode == kModeHT && P.D <= kSortDirsMax) {
+        static const cudaError_t attr = cudaFuncSetAttribute(k_dir_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                             (int)(sizeof(unsigned long long) * kSortDirsMax));
+        if (attr != cudaSuccess) return attr;
+        int L = 1;
+        while (L < P.D) L <<= 1;
+        k_dir_sort<<<P.nsets, 1024, sizeof(unsigned long long) * L, st>>>(P, n);
+        return cudaGetLastError();
+    }
     if (n == 2) k_dir_prep<4><<<P.nsets, 1024, 0, st>>>(P, n);
     else k_dir_prep<8><<<P.nsets, 1024, 0, st>>>(P, n);
     return cudaGetLastError();
@@ -123,8 +201,9 @@ __global__ void __launch_bounds__(1024) k_plan(EvalPlan P, TablesDev t) {
         }
         chunk_sh = chunk;
         carry = 0;
-        P.ctl[0] = 0;
+        P.ctl[0] = 0;   // item counter (second counter ctl[3]: wide hybrid-transform tiles)
         P.ctl[1] = chunk;
+        P.ctl[3] = 0;
     }
     __syncthreads();
     const int chunk = chunk_sh;

@@ -1,0 +1,212 @@
+"""Hybrid transforms and their adjoint over every range of directions the ABI accepts.
+
+The FP32C kernels pick an evaluation path per tile of directions from the tile's largest
+M = sum_k |xi_k| / 2 (a bound on |<xi, v>|): packed FP32 arguments up to M <= 1 (Laplace),
+1.75 (Fourier, sine) or 2 (Bessel), the scalar path with FP64 arguments beyond (and, for
+Laplace, FP64 exponents with per-round rescaling).  Each band of M below is run as its
+own call, so that every tile of the call lands on the path of that band, for one, two,
+four and eight directions per lane, in 2-D and 3-D, forward and adjoint, and checked
+against the oracle (Lemma 3.1 and its derivative) at the library's stated accuracy:
+1e-6 of sum |Delta kbar| per direction (FP32C), 2e-6 of sum |terms| for the adjoint.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_02256_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KERNELS = ["laplace", "fourier", "bessel", "sine"]
+
+# bands of M = sum_k |xi_k| / 2
+BANDS = {
+    "M<=0.75": (0.02, 0.75),
+    "1<M<=1.75": (1.0001, 1.75),
+    "1.75<M<=2": (1.7501, 2.0),
+    "2<M<=pi": (2.0001, math.pi),
+    "pi<M<=14": (math.pi, 14.0),
+}
+
+
+@pytest.fixture(scope="module")
+def tb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_02256_gb300 import binding
+    binding.load()
+    return binding
+
+
+IMAGES = {
+    2: synth.grf((90, 117), 5.0, seed=301),
+    3: synth.grf((14, 19, 23), 3.0, seed=302),
+}
+
+
+def band_dirs(n: int, count: int, seed: int, lo: float, hi: float) -> np.ndarray:
+    """Directions spread over every orthant with sum_k |xi_k| / 2 uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((count, n))
+    g /= np.abs(g).sum(axis=1, keepdims=True)
+    return g * (2.0 * rng.uniform(lo, hi, size=(count, 1)))
+
+
+def _fwd_err(got, want, norm, kernel):
+    if kernel == "fourier":
+        got = got[..., 0] + 1j * got[..., 1]
+    return np.max(np.abs(got - want) / np.maximum(norm, 1e-300))
+
+
+def _adj_check(got, g, gn, gout, kernel):
+    if kernel == "fourier":
+        want = gout[0, :, 0:1] * g.real + gout[0, :, 1:2] * g.imag
+        sc = (np.abs(gout[0, :, 0:1]) + np.abs(gout[0, :, 1:2])) * gn
+    else:
+        want = gout[0][:, None] * g
+        sc = np.abs(gout[0])[:, None] * gn
+    return np.max(np.abs(got - want) / np.maximum(sc, 1e-300))
+
+
+@pytest.mark.parametrize("band", list(BANDS))
+@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_forward_bands(tb, kernel, n, band):
+    img = IMAGES[n]
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    lo, hi = BANDS[band]
+    dirs = band_dirs(n, 72, 310 + n, lo, hi)
+    d = torch.from_numpy(dirs).cuda()
+    want, norm = O.hybrid_transform(ref, kernel, dirs)
+    for dl in ([1, 2, 4, 8] if kernel == "laplace" else [1, 2, 4]):
+        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+        got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
+        assert _fwd_err(got, want, norm, kernel) <= 1e-6, (dl, _fwd_err(got, want, norm, kernel))
+    got = tb.hybrid_transform(tabs, kernel, d, "fp64").cpu().numpy()[0]
+    assert _fwd_err(got, want, norm, kernel) <= 1e-12
+
+
+@pytest.mark.parametrize("band", list(BANDS))
+@pytest.mark.parametrize("n", [2, 3])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_adjoint_bands(tb, kernel, n, band):
+    img = IMAGES[n]
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    lo, hi = BANDS[band]
+    dirs = band_dirs(n, 48, 320 + n, lo, hi)
+    d = torch.from_numpy(dirs).cuda()
+    rng = np.random.default_rng(321)
+    gout = rng.standard_normal((1, 48, 2)) if kernel == "fourier" else rng.standard_normal((1, 48))
+    go = torch.from_numpy(gout).cuda()
+    g, gn = O.hybrid_transform_grad(ref, kernel, dirs)
+    dls = [1, 2] if kernel == "fourier" else ([1, 2, 4] if n == 2 else [1, 2])
+    for dl in dls:
+        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+        got = tb.hybrid_transform_grad(tabs, kernel, d, go).cpu().numpy()
+        assert _adj_check(got, g, gn, gout, kernel) <= 2e-6, (dl, _adj_check(got, g, gn, gout, kernel))
+    got = tb.hybrid_transform_grad(tabs, kernel, d, go, "fp64").cpu().numpy()
+    assert _adj_check(got, g, gn, gout, kernel) <= 1e-11
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_mixed_bands_one_call(tb, kernel):
+    """One call whose orthants hold tiles of every band: both launches share the items."""
+    img = IMAGES[2]
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    dirs = np.concatenate([band_dirs(2, 40, 330 + i, lo, hi) for i, (lo, hi) in enumerate(BANDS.values())])
+    d = torch.from_numpy(dirs).cuda()
+    want, norm = O.hybrid_transform(ref, kernel, dirs)
+    for dl in (2, 4):
+        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+        got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
+        assert _fwd_err(got, want, norm, kernel) <= 1e-6
+
+
+def test_laplace_large_m(tb):
+    """Laplace with M up to 250: FP64 exponents and rescaled rounds; beyond 300, NaN."""
+    img = IMAGES[2]
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    dirs = np.concatenate([band_dirs(2, 24, 340, 20.0, 60.0), band_dirs(2, 24, 341, 100.0, 250.0)])
+    want, norm = O.hybrid_transform(ref, "laplace", dirs)
+    for dl in (1, 4, 8):
+        tabs.set_tuning(ht_dirs_per_lane=dl)
+        got = tb.hybrid_transform(tabs, "laplace", torch.from_numpy(dirs).cuda()).cpu().numpy()[0]
+        assert np.max(np.abs(got - want) / norm) <= 1e-6
+    over = torch.tensor([[400.0, 300.0], [0.5, 0.25]], dtype=torch.float64, device="cuda")
+    got = tb.hybrid_transform(tabs, "laplace", over).cpu().numpy()[0]
+    assert math.isnan(got[0]) and math.isfinite(got[1])
+
+
+def test_worked_example_fp32c_every_kernel(tb, golden):
+    """xi = (2, 2) on the running example (Appendix A): M = 2, so Laplace and Fourier take
+    the scalar path; Laplace reproduces the closed form 2 e^{-2/3} - e^{2/3} - e^{4/3}."""
+    img = np.array(golden["image"], dtype=np.uint8)
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    xi = np.array([golden["ect"]["xi"]], dtype=np.float64)
+    d = torch.from_numpy(xi).cuda()
+    exact = 2 * math.exp(-2 / 3) - math.exp(2 / 3) - math.exp(4 / 3)
+    for dl in (1, 2, 4):
+        tabs.set_tuning(ht_dirs_per_lane=dl)
+        for kernel in KERNELS:
+            got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
+            want, norm = O.hybrid_transform(ref, kernel, xi)
+            assert _fwd_err(got, want, norm, kernel) <= 1e-6, kernel
+            if kernel == "laplace":
+                assert abs(got[0] - exact) <= 1e-6 * norm[0]
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_table_kernel_wide_directions(tb, n):
+    """A tabulated kernel under directions up to |<xi, v>| ~ 14, beyond the table's
+    span on both sides.  Bound: 1e-6 sum |Delta kbar| plus the FP32 position error,
+    2^-21 (b - a) sum |Delta kappa| (a few units of 2^-24 in a position scaled to [0, 1])."""
+    img = IMAGES[n]
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    a, b, K = -10.0, 10.0, 2049
+    s = np.linspace(a, b, K)
+    vals = np.tanh(0.25 * s) + 0.5 * np.sin(0.5 * s)
+    kt = tb.KernelTable(vals, a, b)
+    kern = O.table_kernel(vals, a, b)
+    dirs = np.concatenate([band_dirs(n, 40, 350, 0.05, 1.0), band_dirs(n, 40, 351, 2.0, 14.0)])
+    want, norm = O.hybrid_transform(ref, kern, dirs)
+    # sum |Delta kappa| per direction
+    half = 1 << (n - 1)
+    slope = np.zeros(len(dirs))
+    for i, xi in enumerate(dirs):
+        o = O.orthant_of(xi)
+        r = o if o < half else O.partner(o, n)
+        sv = O.dot_products(xi, ref.delta_idx[r], ref.m)
+        slope[i] = np.sum(np.abs(ref.delta_val[r]) * np.abs(kern[1](sv)))
+    bound = 1e-6 * norm + 2.0 ** -21 * (b - a) * slope
+    for dl in (1, 2, 4):
+        tabs.set_tuning(ht_dirs_per_lane=dl)
+        got = tb.hybrid_transform(tabs, kt, torch.from_numpy(dirs).cuda()).cpu().numpy()[0]
+        assert np.all(np.abs(got - want) <= bound), dl
+    got = tb.hybrid_transform(tabs, kt, torch.from_numpy(dirs).cuda(), "fp64").cpu().numpy()[0]
+    assert np.max(np.abs(got - want) / norm) <= 1e-12
+    kt.free()
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "fourier", "bessel"])
+def test_error_relative_to_output(tb, kernel):
+    """max |GPU - oracle| / max |oracle| <= 1e-6 on a GRF image with the bench's direction
+    law (|xi| log-uniform in [0.01, 1]), where kbar(s) - kbar(0) keeps small transforms
+    accurate."""
+    img = synth.grf((256, 256), 16.0, seed=360)
+    ref = O.critical_tables(img)
+    tabs = tb.build_critical_tables(tb.pack_images([img]))
+    dirs = synth.random_2d_dirs(512, 361, 0.01, 1.0)
+    want, _ = O.hybrid_transform(ref, kernel, dirs)
+    got = tb.hybrid_transform(tabs, kernel, torch.from_numpy(dirs).cuda()).cpu().numpy()[0]
+    if kernel == "fourier":
+        got = got[..., 0] + 1j * got[..., 1]
+    assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= 1e-6
