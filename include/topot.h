@@ -128,6 +128,35 @@ TOPOT_API topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_
                            const int64_t* h_offsets, int B,
                            topot_construction construction, topot_tables** out);
 
+/* Slabs of volumes (the paper parallelises the preprocessing over vertex subsets and the
+ * evaluation over directions, Section 5.3).  As tables_create for 3-D images (n = 3,
+ * vertex construction, else UNSUPPORTED), where image b is the part of a volume of shape
+ * h_shapes[b] (m_0, m_1, m_2: the WHOLE volume) made of the planes
+ * z in [z0, z1) = [h_zrange[2b], h_zrange[2b+1]) (0 <= z0 < z1 <= m_2, else INVALID_ARG).
+ * Its pixel buffer (at h_offsets[b]) holds planes max(z0 - 1, 0) .. min(z1 + 1, m_2) - 1:
+ * the slab and the neighbouring plane on each side that exists (staged for the stencil,
+ * owned by the neighbouring slab).  The handle's tables hold the owned vertices only,
+ * with their linear index in the whole volume and the volume's embedding; chi and
+ * sum |Delta^-| (tables_info) are the slab's parts.  Every transform of a slab handle is
+ * the slab's part of the volume's transform: ECT and Radon of the slabs of a partition of
+ * [0, m_2) sum exactly to the volume's, hybrid transforms and gradients to within their
+ * accuracy (slab_sum_i32 / slab_sum_f64 add the parts in slab order).  Exact
+ * representations of a slab handle represent the slab's part. */
+TOPOT_API topot_status tables_create_slab(topot_dtype dtype, int n, const int64_t* h_shapes,
+                                          const int64_t* h_offsets, const int64_t* h_zrange, int B,
+                                          topot_tables** out);
+
+/* Sums of slab parts, in slab order (Section 5.3; the exchange step of a volume split
+ * across devices).  d_parts is [P][n] (P >= 1 parts of n elements each, for example the
+ * ECT, Radon or hybrid outputs of P slabs gathered from P devices), d_out [n].
+ *   slab_sum_i32: exact integer sums; *d_overflow (device, caller-owned) is set to 0 and
+ *     then to 1 if some sum leaves the int32 range (that element is written as 0).
+ *   slab_sum_f64: compensated (Neumaier) FP64 sums in slab order, deterministic.
+ * Asynchronous on `stream`; INVALID_ARG on NULL pointers or bad sizes. */
+TOPOT_API topot_status slab_sum_i32(const int32_t* d_parts, int P, int64_t n, int32_t* d_out,
+                                    uint32_t* d_overflow, void* stream);
+TOPOT_API topot_status slab_sum_f64(const double* d_parts, int P, int64_t n, double* d_out, void* stream);
+
 /* Enqueue the extraction of all tables of `t` from d_pixels on `stream`
  * (asynchronous, no allocation, no host synchronisation: may be captured in a
  * CUDA graph once the handle exists).  Table sizes stay on the device; the
@@ -260,9 +289,14 @@ TOPOT_API topot_status hybrid_transform_grad(const topot_tables* t, topot_kernel
  * that disallows cudaMalloc after start-up) can call this entry point instead.
  * Arguments and result are those of hybrid_transform(); the handle's device must be
  * current.  Its scratch (work plan and partial sums) lives in one fixed 16 MiB device
- * array that every GPU loading the library holds until the process exits; the first
- * call on a device looks the array's address up (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  It calls no cudaMalloc / cudaFree.  A call
+ * array that every GPU loading the library holds until the process exits.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress); with CUDA's lazy
+ * module loading (the default) that first call also loads the library's device code on
+ * that device, which is when the 16 MiB are reserved.  So make the first call during
+ * start-up, outside any context that forbids allocation, and before any stream capture;
+ * later calls reserve nothing and call no cudaMalloc / cudaFree.  The address is kept per
+ * device for the life of the process: after cudaDeviceReset the device code is reloaded
+ * elsewhere, so do not call this entry point on a device that has been reset.  A call
  * whose scratch would exceed 16 MiB returns TOPOT_ERR_INVALID_ARG with the size in the
  * message.  All calls on a device share the array: calls that may overlap on the GPU
  * (different streams, no ordering) race and must be serialised by the caller. */

@@ -29,7 +29,7 @@ API_SYMBOLS = (
     "tables_copy_to_host", "tables_set_tuning", "free_tables", "ect", "radon", "hybrid_transform",
     "hybrid_transform_grad", "hybrid_transform_noalloc", "exact_representation", "ect_exact_eval",
     "radon_exact_eval", "topot_selftest_wait", "topot_last_error", "kernel_table_create", "kernel_table_free",
-    "hybrid_transform_table", "hybrid_transform_table_grad",
+    "hybrid_transform_table", "hybrid_transform_table_grad", "tables_create_slab", "slab_sum_i32", "slab_sum_f64",
 )
 
 
@@ -81,6 +81,9 @@ def load(path: str = LIB_PATH):
         "kernel_table_create": [vp, i32, dp, dp, pp],
         "hybrid_transform_table": [vp, vp, i32, vp, i32, i32, vp, vp],
         "hybrid_transform_table_grad": [vp, vp, i32, vp, i32, i32, vp, vp, vp],
+        "tables_create_slab": [i32, i32, i64p, i64p, i64p, i32, pp],
+        "slab_sum_i32": [vp, i32, ctypes.c_int64, vp, vp, vp],
+        "slab_sum_f64": [vp, i32, ctypes.c_int64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -254,6 +257,38 @@ def tables_create(shapes, offsets, dtype=U8, construction: str = "vertex") -> Ta
     _check(load().tables_create(dtype, shapes.shape[1], _i64(shapes), _i64(offsets), shapes.shape[0],
                                 CONSTRUCTIONS[construction], ctypes.byref(h)))
     return Tables(h, shapes.shape[1], shapes.shape[0], dtype, shapes, offsets)
+
+
+def tables_create_slab(shapes, offsets, zrange, dtype=U8) -> Tables:
+    """A handle for slabs of volumes: image b is planes [zrange[b][0], zrange[b][1]) of a
+    volume of shape shapes[b] (axis 0 fastest); its pixels hold the slab plus the
+    neighbouring plane on each side that exists (paper_2405_02256_gb300.slabs packs them)."""
+    shapes = np.asarray(shapes, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(load().tables_create_slab(dtype, shapes.shape[1], _i64(shapes), _i64(offsets), _i64(zrange),
+                                     shapes.shape[0], ctypes.byref(h)))
+    return Tables(h, shapes.shape[1], shapes.shape[0], dtype, shapes, offsets)
+
+
+def slab_sum(parts: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """Sum of P slab parts [P, ...] in slab order: exact for int32 (TopotError OVERFLOW if a
+    sum leaves the int32 range), compensated for float64.  Returns [...]."""
+    parts = parts.contiguous()
+    P = parts.shape[0]
+    n = parts[0].numel()
+    if out is None:
+        out = torch.empty(parts.shape[1:], dtype=parts.dtype, device=parts.device)
+    L = load()
+    if parts.dtype == torch.int32:
+        flag = torch.zeros(1, dtype=torch.int32, device=parts.device)
+        _check(L.slab_sum_i32(_ptr(parts), P, n, _ptr(out), _ptr(flag), _stream(stream)))
+        if int(flag.item()) != 0:
+            raise TopotError(5, "slab_sum: a sum leaves the int32 range")
+    elif parts.dtype == torch.float64:
+        _check(L.slab_sum_f64(_ptr(parts), P, n, _ptr(out), _stream(stream)))
+    else:
+        raise ValueError("slab parts must be int32 or float64")
+    return out
 
 
 def ect(tables: Tables, dirs: torch.Tensor, t_min: float, t_max: float, T: int, out=None, stream=None):

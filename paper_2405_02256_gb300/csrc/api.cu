@@ -12,6 +12,11 @@
 
 namespace topot {
 cudaError_t launch_extract(int n, topot_dtype dtype, bool top, const ExtractArgs& a, cudaStream_t st);
+cudaError_t launch_segment_sums(const TablesDev& t, long long* vsum, cudaStream_t st);
+cudaError_t launch_slab_sum_i32(const int32_t* parts, int P, long long n, int32_t* out, unsigned* err, int sm_count,
+                                cudaStream_t st);
+cudaError_t launch_slab_sum_f64(const double* parts, int P, long long n, double* out, int sm_count,
+                                cudaStream_t st);
 cudaError_t launch_top_prepass(const void* pixels, topot_dtype dtype, int32_t* V, const TopSrc* src, int B, int n,
                                long long max_nv, int sm_count, cudaStream_t st);
 int extract_block(int n);
@@ -31,7 +36,7 @@ cudaError_t launch_hist_finish(int mode, int B, int D, int T, const long long* c
 cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
                       int grid, double* part, cudaStream_t st);
 cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
-                              const double* part, double* out, cudaStream_t st);
+                              const double* part, const long long* vsum, int S, double* out, cudaStream_t st);
 cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
                                   const double* part, const double* gout, double* gdirs, cudaStream_t st);
 }  // namespace topot
@@ -70,7 +75,9 @@ struct topot_tables {
     unsigned* err = nullptr;
     unsigned* ticket = nullptr;
     unsigned long long* status = nullptr;
-    size_t clear_bytes = 0;           // bytes from `chi` to the end of `status` zeroed per build
+    long long* vsum = nullptr;        // [B][S] sum of the values of each table (slabs)
+    bool slab = false;                // tables of slabs of volumes (tables_create_slab)
+    size_t clear_bytes = 0;           // bytes from `chi` to the end of `vsum` zeroed per build
     int* arena_idx = nullptr;
     void* arena_val = nullptr;
     // host copies (valid after tables_sync)
@@ -171,10 +178,17 @@ extern "C" {
 
 const char* topot_last_error(void) { return g_last_error.c_str(); }
 
-topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, const int64_t* h_offsets, int B,
-                           topot_construction construction, topot_tables** out) {
+}  // extern "C"
+
+// tables_create and tables_create_slab: h_zrange (NULL for whole images) gives per image
+// the owned planes [z0, z1) of a volume.
+static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shapes, const int64_t* h_offsets,
+                                const int64_t* h_zrange, int B, topot_construction construction,
+                                topot_tables** out) {
     if (!out) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: out is NULL");
     *out = nullptr;
+    if (h_zrange && (n != 3 || construction != TOPOT_VERTEX))
+        return fail(TOPOT_ERR_UNSUPPORTED, "tables_create_slab: slabs of 3-D volumes, vertex construction only");
     if (construction != TOPOT_VERTEX && construction != TOPOT_TOP)
         return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad construction");
     if (dtype != TOPOT_U8 && dtype != TOPOT_I32) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad dtype");
@@ -229,6 +243,21 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
             delete t;
             return fail(TOPOT_ERR_INVALID_ARG, "tables_create: an image must have < 2^31 vertices and offset >= 0");
         }
+        // owned planes: all, or the slab [z0, z1) whose pixels start at plane max(z0 - 1, 0)
+        I.zlo = 0;
+        I.zbase = 0;
+        I.nz = I.m[2];
+        if (h_zrange) {
+            const int64_t z0 = h_zrange[2 * (long long)b], z1 = h_zrange[2 * (long long)b + 1];
+            if (z0 < 0 || z1 <= z0 || z1 > I.m[2]) {
+                delete t;
+                return fail(TOPOT_ERR_INVALID_ARG, "tables_create_slab: need 0 <= z0 < z1 <= m_2");
+            }
+            I.zlo = (int)z0;
+            I.zbase = z0 > 0 ? (int)z0 - 1 : 0;
+            I.nz = (int)(z1 - z0);
+            N = (long long)I.m[0] * I.m[1] * I.nz;   // owned vertices: the capacity of a table
+        }
         if (top) {
             // corner images start at multiples of 4 elements (16 bytes)
             h_top[b].pix_offset = h_offsets[b];
@@ -266,7 +295,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
         }
         I.segs_per_row = (m0 + I.W - 1) / I.W;
         I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
-        tiles += (long long)I.tiles_per_plane * I.m[2];
+        tiles += (long long)I.tiles_per_plane * I.nz;
         for (int k = 0; k < kMaxDim; ++k) I.inv2m[k] = I.m[k] > 1 ? 0.5 / (double)(I.m[k] - 1) : 0.0;
         I.div0 = make_fastdiv((uint32_t)m0);
         I.div1 = make_fastdiv((uint32_t)m1);
@@ -296,6 +325,7 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
     const size_t o_abs = place(sizeof(long long) * B * t->NO);
     const size_t o_tic = place(sizeof(unsigned));
     const size_t o_sta = place(sizeof(unsigned long long) * tiles * t->S);
+    const size_t o_vsum = place(sizeof(long long) * B * t->S);
     const size_t meta_bytes = off;
     e = cudaMalloc(&t->meta, meta_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&t->arena_idx, sizeof(int) * (size_t)entries);
@@ -312,6 +342,8 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
     t->absum = reinterpret_cast<long long*>(m + o_abs);
     t->ticket = reinterpret_cast<unsigned*>(m + o_tic);
     t->status = reinterpret_cast<unsigned long long*>(m + o_sta);
+    t->vsum = reinterpret_cast<long long*>(m + o_vsum);
+    t->slab = h_zrange != nullptr;
     t->clear_bytes = meta_bytes - o_chi;
     if (top) {
         const size_t src_bytes = align_up(sizeof(TopSrc) * B, 256);
@@ -344,6 +376,19 @@ topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, co
     return TOPOT_OK;
 }
 
+extern "C" {
+
+topot_status tables_create(topot_dtype dtype, int n, const int64_t* h_shapes, const int64_t* h_offsets, int B,
+                           topot_construction construction, topot_tables** out) {
+    return create_impl(dtype, n, h_shapes, h_offsets, nullptr, B, construction, out);
+}
+
+topot_status tables_create_slab(topot_dtype dtype, int n, const int64_t* h_shapes, const int64_t* h_offsets,
+                                const int64_t* h_zrange, int B, topot_tables** out) {
+    if (!h_zrange) return fail(TOPOT_ERR_INVALID_ARG, "tables_create_slab: h_zrange is NULL");
+    return create_impl(dtype, n, h_shapes, h_offsets, h_zrange, B, TOPOT_VERTEX, out);
+}
+
 topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     if (!t || !d_pixels) return fail(TOPOT_ERR_INVALID_ARG, "tables_build: NULL argument");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -368,6 +413,9 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     } else {
         TOPOT_CUDA(launch_extract(t->n, t->dtype, false, a, st));
     }
+    // a slab's tables need not sum to zero: their value sums let the hybrid transforms
+    // put back the constant kbar(0) that the FP32C kernels leave out
+    if (t->slab) TOPOT_CUDA(launch_segment_sums(t->dev(), t->vsum, st));
     return TOPOT_OK;
 }
 
@@ -556,6 +604,84 @@ topot_status radon(const topot_tables* t, const double* d_dirs, int D, int per_i
 
 // ---- hybrid transforms ----------------------------------------------------------------------
 
+// Tile and chunk choices of one hybrid-transform call, and the scratch they need.  Both
+// hybrid_transform (workspace grown with cudaMalloc) and hybrid_transform_noalloc (fixed
+// array) size and carve their scratch through these two functions, so that the two give
+// the same result for the same call.
+struct HtSizing {
+    int dl = 1;               // directions per lane
+    int tdh = 32;             // directions per tile
+    int ncomp = 1;            // FP64 partials per direction and item
+    int npairs = 0;
+    int target = 0;           // automatic chunking aims at about this many items
+    long long max_items = 0;  // capacity of the per-item partials
+    size_t part_elems = 0;
+    size_t need = 0;          // scratch bytes (plan + partials + alignment slack)
+};
+
+static HtSizing ht_sizing(const topot_tables* t, topot_kernel kernel, topot_precision precision, int D,
+                          int per_image_dirs, bool adjoint) {
+    HtSizing z;
+    const int nsets = per_image_dirs ? t->B : 1;
+    const int NO = t->NO;
+    if (precision == TOPOT_FP32C) {
+        z.dl = t->tuning.ht_dirs_per_lane;
+        const int per_orthant = D / NO;
+        if (z.dl == 0) {
+            z.dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+            if (kernel == TOPOT_LAPLACE && per_orthant >= 256) z.dl = 8;
+        }
+        if (z.dl == 8 && kernel != TOPOT_LAPLACE) z.dl = 4;
+        // adjoint: two direction pairs per lane for the one-component kernels in 2-D, else one
+        if (adjoint && kernel != TOPOT_TABLE)
+            z.dl = std::min(z.dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
+    }
+    z.tdh = 32 * z.dl;
+    const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
+    z.ncomp = adjoint ? nk * t->n : nk;
+    z.npairs = t->B * NO;
+    z.target = t->sm_count * 16;
+    if (t->tuning.ht_chunk > 0) {
+        for (int b = 0; b < t->B; ++b)
+            z.max_items += (long long)((D + z.tdh - 1) / z.tdh + NO) *
+                           ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
+    } else {
+        z.max_items = z.target + (long long)t->B * ((D + z.tdh - 1) / z.tdh + NO);
+    }
+    z.part_elems = (size_t)z.max_items * z.tdh * z.ncomp;
+    z.need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
+             sizeof(long long) * (z.npairs + 1) + sizeof(int) * z.npairs + sizeof(double) * z.part_elems + 8 * 256;
+    return z;
+}
+
+// Lays the plan and the partials of a call out in `scratch` (at least z.need bytes).  Every
+// field is written by the planning kernels before it is read, so old contents are harmless.
+static EvalPlan ht_carve(const topot_tables* t, const HtSizing& z, const double* d_dirs, int D, int per_image_dirs,
+                         void* scratch, double** part) {
+    const int nsets = per_image_dirs ? t->B : 1;
+    Carver cv{reinterpret_cast<char*>(scratch)};
+    EvalPlan P{};
+    P.mode = kModeHT;
+    P.nsets = nsets;
+    P.D = D;
+    P.tile_dirs = z.tdh;
+    P.chunk_req = t->tuning.ht_chunk;
+    P.target_items = z.target;
+    P.npairs = z.npairs;
+    P.max_items = z.max_items;
+    P.dirs = d_dirs;
+    P.ctl = cv.take<int>(4);
+    P.perm = cv.take<int>((size_t)nsets * D);
+    P.rank = cv.take<int>((size_t)nsets * D);
+    P.boff = cv.take<int>((size_t)nsets * (t->NO + 1));
+    P.pair_items = cv.take<long long>(z.npairs + 1);
+    P.pair_chunks = cv.take<int>(z.npairs);
+    P.thr = nullptr;
+    P.T = 0;
+    *part = cv.take<double>(z.part_elems);
+    return P;
+}
+
 static topot_status ht_common(const char* name, const topot_tables* tc, topot_kernel kernel,
                               topot_precision precision, const double* d_dirs, int D, int per_image_dirs,
                               bool adjoint, const double* d_gout, double* d_out, void* stream,
@@ -573,58 +699,11 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     if (precision != TOPOT_FP32C && precision != TOPOT_FP64)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int nsets = per_image_dirs ? t->B : 1;
-    const int NO = t->NO;
-    int dl = 1;
-    if (precision == TOPOT_FP32C) {
-        dl = t->tuning.ht_dirs_per_lane;
-        const int per_orthant = D / NO;
-        if (dl == 0) {
-            dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
-            if (kernel == TOPOT_LAPLACE && per_orthant >= 256) dl = 8;
-        }
-        if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
-        // adjoint: two direction pairs per lane for the one-component kernels in 2-D, else one
-        if (adjoint && kernel != TOPOT_TABLE) dl = std::min(dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
-    }
-    const int tdh = 32 * dl;
-    const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
-    const int ncomp = adjoint ? nk * t->n : nk;
-    const int npairs = t->B * NO;
-    const int target = t->sm_count * 16;
-    long long max_items;
-    if (t->tuning.ht_chunk > 0) {
-        max_items = 0;
-        for (int b = 0; b < t->B; ++b)
-            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
-    } else {
-        max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
-    }
-    const size_t part_elems = (size_t)max_items * tdh * ncomp;
-    const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
-                        sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * part_elems +
-                        8 * 256;
-    topot_status s = ensure_ws(t, need);
+    const HtSizing z = ht_sizing(t, kernel, precision, D, per_image_dirs, adjoint);
+    topot_status s = ensure_ws(t, z.need);
     if (s != TOPOT_OK) return s;
-    Carver cv{reinterpret_cast<char*>(t->ws)};
-    EvalPlan P{};
-    P.mode = kModeHT;
-    P.nsets = nsets;
-    P.D = D;
-    P.tile_dirs = tdh;
-    P.chunk_req = t->tuning.ht_chunk;
-    P.target_items = target;
-    P.npairs = npairs;
-    P.max_items = max_items;
-    P.dirs = d_dirs;
-    P.ctl = cv.take<int>(4);
-    P.perm = cv.take<int>((size_t)nsets * D);
-    P.rank = cv.take<int>((size_t)nsets * D);
-    P.boff = cv.take<int>((size_t)nsets * (NO + 1));
-    P.pair_items = cv.take<long long>(npairs + 1);
-    P.pair_chunks = cv.take<int>(npairs);
-    P.thr = nullptr;
-    P.T = 0;
+    double* part = nullptr;
+    EvalPlan P = ht_carve(t, z, d_dirs, D, per_image_dirs, t->ws, &part);
     if (kernel == TOPOT_TABLE) {
         P.ktab = kt->d32;
         P.ktab64 = kt->d64;
@@ -632,7 +711,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
         P.ktab_a = kt->a;
         P.ktab_h = kt->h;
     }
-    double* part = cv.take<double>(part_elems);
+    const int dl = z.dl, tdh = z.tdh;
 
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
@@ -641,7 +720,8 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     if (adjoint)
         TOPOT_CUDA(launch_ht_adj_combine(P, t->n, t->B, kernel, precision, tdh, part, d_gout, d_out, st));
     else
-        TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, d_out, st));
+        TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, t->slab ? t->vsum : nullptr,
+                                     t->S, d_out, st));
     return TOPOT_OK;
 }
 
@@ -786,71 +866,58 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
     if (dev != t->device)
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": the handle's device must be current");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int nsets = per_image_dirs ? t->B : 1;
-    const int NO = t->NO;
-    // same tile and chunk choices as hybrid_transform, hence the same result
-    int dl = 1;
-    if (precision == TOPOT_FP32C) {
-        dl = t->tuning.ht_dirs_per_lane;
-        const int per_orthant = D / NO;
-        if (dl == 0) {
-            dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
-            if (kernel == TOPOT_LAPLACE && per_orthant >= 256) dl = 8;
-        }
-        if (dl == 8 && kernel != TOPOT_LAPLACE) dl = 4;
-    }
-    const int tdh = 32 * dl;
-    const int ncomp = kernel == TOPOT_FOURIER ? 2 : 1;
-    const int npairs = t->B * NO;
-    const int target = t->sm_count * 16;
-    long long max_items;
-    if (t->tuning.ht_chunk > 0) {
-        max_items = 0;
-        for (int b = 0; b < t->B; ++b)
-            max_items += (long long)((D + tdh - 1) / tdh + NO) * ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
-    } else {
-        max_items = target + (long long)t->B * ((D + tdh - 1) / tdh + NO);
-    }
-    const size_t part_elems = (size_t)max_items * tdh * ncomp;
-    const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
-                        sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * part_elems +
-                        8 * 256;
-    if (need > kNoAllocScratchBytes)
+    // the tile and chunk choices of hybrid_transform (shared helper), hence its result
+    const HtSizing z = ht_sizing(t, kernel, precision, D, per_image_dirs, false);
+    if (z.need > kNoAllocScratchBytes)
         return fail(TOPOT_ERR_INVALID_ARG,
-                    std::string(name) + ": this call needs " + std::to_string(need) +
+                    std::string(name) + ": this call needs " + std::to_string(z.need) +
                         " bytes of scratch, more than the fixed " + std::to_string(kNoAllocScratchBytes) +
                         "; use fewer directions or images per call, or hybrid_transform");
     void* scratch = nullptr;
     topot_status s = noalloc_scratch(&scratch);
     if (s != TOPOT_OK) return s;
-    // Every field below is written by the planning kernels before it is read, so the
-    // previous call's contents need no clearing.
-    Carver cv{reinterpret_cast<char*>(scratch)};
-    EvalPlan P{};
-    P.mode = kModeHT;
-    P.nsets = nsets;
-    P.D = D;
-    P.tile_dirs = tdh;
-    P.chunk_req = t->tuning.ht_chunk;
-    P.target_items = target;
-    P.npairs = npairs;
-    P.max_items = max_items;
-    P.dirs = d_dirs;
-    P.ctl = cv.take<int>(4);
-    P.perm = cv.take<int>((size_t)nsets * D);
-    P.rank = cv.take<int>((size_t)nsets * D);
-    P.boff = cv.take<int>((size_t)nsets * (NO + 1));
-    P.pair_items = cv.take<long long>(npairs + 1);
-    P.pair_chunks = cv.take<int>(npairs);
-    P.thr = nullptr;
-    P.T = 0;
-    double* part = cv.take<double>(part_elems);
+    double* part = nullptr;
+    EvalPlan P = ht_carve(t, z, d_dirs, D, per_image_dirs, scratch, &part);
+    const int dl = z.dl, tdh = z.tdh;
 
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
     const int per_sm = t->tuning.ht_ctas_per_sm > 0 ? t->tuning.ht_ctas_per_sm : 4;
     TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, false, dl, t->sm_count * per_sm, part, st));
-    TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, d_out, st));
+    TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, t->slab ? t->vsum : nullptr, t->S,
+                                 d_out, st));
+    return TOPOT_OK;
+}
+
+}  // extern "C"
+
+// ---- sums over slabs -----------------------------------------------------------------------
+
+static int current_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 1;
+    return std::max(sms, 1);
+}
+
+extern "C" {
+
+topot_status slab_sum_i32(const int32_t* d_parts, int P, int64_t n, int32_t* d_out, uint32_t* d_overflow,
+                          void* stream) {
+    if (!d_parts || !d_out || !d_overflow || P < 1 || n < 0)
+        return fail(TOPOT_ERR_INVALID_ARG, "slab_sum_i32: bad pointers or sizes");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    TOPOT_CUDA(cudaMemsetAsync(d_overflow, 0, sizeof(uint32_t), st));
+    if (n == 0) return TOPOT_OK;
+    TOPOT_CUDA(launch_slab_sum_i32(d_parts, P, n, d_out, d_overflow, current_sm_count(), st));
+    return TOPOT_OK;
+}
+
+topot_status slab_sum_f64(const double* d_parts, int P, int64_t n, double* d_out, void* stream) {
+    if (!d_parts || !d_out || P < 1 || n < 0) return fail(TOPOT_ERR_INVALID_ARG, "slab_sum_f64: bad pointers or sizes");
+    if (n == 0) return TOPOT_OK;
+    TOPOT_CUDA(launch_slab_sum_f64(d_parts, P, n, d_out, current_sm_count(), reinterpret_cast<cudaStream_t>(stream)));
     return TOPOT_OK;
 }
 

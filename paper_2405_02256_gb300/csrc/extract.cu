@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     const ImgDesc I = T.img[b];
     const int m0 = I.m[0], m1 = I.m[1], m2 = I.m[2];
     const long long lt = ticket - I.tile_begin;
-    const long long ntiles_img = (long long)I.tiles_per_plane * m2;
-    const int z = (int)(lt / I.tiles_per_plane);
-    const int rem = (int)(lt - (long long)z * I.tiles_per_plane);
+    const long long ntiles_img = (long long)I.tiles_per_plane * I.nz;
+    const int zl = (int)(lt / I.tiles_per_plane);   // owned plane; volume plane z (slabs: zlo + zl)
+    const int z = I.zlo + zl;
+    const int rem = (int)(lt - (long long)zl * I.tiles_per_plane);
     const int rb = rem / I.segs_per_row;
     const int sg = rem - rb * I.segs_per_row;
     const int y0 = rb * I.R;
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     const long long L0 = ((long long)z * m1 + y0) * m0 + x0;
 
     // ---- 1. stage pixels + halo -------------------------------------------------------
-    const Tin* img = reinterpret_cast<const Tin*>(p.pixels) + I.offset;
+    // pixels of plane zz at img + zz m_1 m_0: the buffer starts at plane zbase (a slab)
+    const Tin* img = reinterpret_cast<const Tin*>(p.pixels) + I.offset - (long long)I.zbase * m1 * m0;
     const int RS = p.row_stride;
     const int PS = p.stage_rows * RS;
     const int srows = rows + 2;

@@ -262,7 +262,7 @@ __device__ __forceinline__ FastDiv ldg_fastdiv(const FastDiv* f) {
 
 // Geometry of one tile (image b, local tile index lt).
 struct TileGeo {
-    int m0, m1, m2, W, R, spr, RS, segs, tpp, lt, z, y0, x0, rows, cols, packed;
+    int m0, m1, m2, W, R, spr, RS, segs, tpp, lt, z, nz, y0, x0, rows, cols, packed;
     long long tile_begin;
     const uint8_t* img;
 };
@@ -283,15 +283,19 @@ __device__ __forceinline__ TileGeo tile_geometry(const ExtractArgs& p, int b, lo
     g.packed = __ldg(&Ip->packed);
     g.tile_begin = __ldg(&Ip->tile_begin);
     g.lt = (int)(ticket - g.tile_begin);
-    g.z = NDIM == 3 ? (int)fastdiv((uint32_t)g.lt, ldg_fastdiv(&Ip->div_tpp)) : 0;
-    const int rem = g.lt - g.z * g.tpp;
+    const int zl = NDIM == 3 ? (int)fastdiv((uint32_t)g.lt, ldg_fastdiv(&Ip->div_tpp)) : 0;   // owned plane
+    g.z = NDIM == 3 ? __ldg(&Ip->zlo) + zl : 0;                                            // volume plane
+    g.nz = NDIM == 3 ? __ldg(&Ip->nz) : 1;
+    const int rem = g.lt - zl * g.tpp;
     const int rb = (int)fastdiv((uint32_t)rem, ldg_fastdiv(&Ip->div_segs));
     const int sg = rem - rb * g.segs;
     g.y0 = rb * g.R;
     g.x0 = sg * g.W;
     g.rows = min(g.R, g.m1 - g.y0);
     g.cols = min(g.W, g.m0 - g.x0);
-    g.img = reinterpret_cast<const uint8_t*>(p.pixels) + __ldg(&Ip->offset);
+    // pixels of plane zz at img + zz m_1 m_0: the buffer starts at plane zbase (a slab)
+    g.img = reinterpret_cast<const uint8_t*>(p.pixels) + __ldg(&Ip->offset) -
+            (NDIM == 3 ? (long long)__ldg(&Ip->zbase) * g.m1 * g.m0 : 0ll);
     return g;
 }
 
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
         if (lane < kSeg) {
             const long long N = __ldg(&Ip->N);
             sh_pref[lane] = __ldg(&Ip->seg_base) + (long long)lane * N + pre;
-            if (lt == tpp * m2 - 1) T.seg_count[(long long)b * kSeg + lane] = (long long)(pre + agg);
+            if (lt == tpp * G.nz - 1) T.seg_count[(long long)b * kSeg + lane] = (long long)(pre + agg);
         }
     } else {
         asm volatile("bar.sync 1, %0;" ::"r"(kB) : "memory");

@@ -1298,8 +1298,12 @@ __device__ __forceinline__ void gather_partials(const EvalPlan& P, int NO, int t
     }
 }
 
+// vsum (slab handles only, else NULL): the value sums of the tables.  The FP32C kernels
+// sum Delta (kbar(s) - kbar(0)) for Fourier's imaginary part, sine and Bessel, which is
+// the transform when the table sums to zero (a whole image); a slab's table need not,
+// and kbar(0) times its sum is added back here (kbar(0) = 1 for cos and J0).
 __global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision, int tdh,
-                             const double* part, double* out) {
+                             const double* part, const long long* vsum, int S, double* out) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)B * P.D) return;
     const int b = (int)(gid / P.D), d = (int)(gid - (long long)b * P.D);
@@ -1310,6 +1314,11 @@ __global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision
     const int nc = kernel == TOPOT_FOURIER ? 2 : 1;
     double v[2];
     gather_partials(P, NO, tdh, nc, b, d, o, part, v);
+    if (vsum && precision == TOPOT_FP32C &&
+        (kernel == TOPOT_FOURIER || kernel == TOPOT_SINE || kernel == TOPOT_BESSEL)) {
+        const int rep = (o & (NO >> 1)) ? (o ^ (NO - 1)) : o;
+        v[nc - 1] += (double)vsum[(long long)b * S + NO + rep];   // cos / J0 component
+    }
     const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
     // sine: the partials hold sum v (cos s - 1), kbar = -cos
     double scale = kernel == TOPOT_SINE ? -sign : sign;
@@ -1465,9 +1474,10 @@ cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int pre
 }
 
 cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
-                              const double* part, double* out, cudaStream_t st) {
+                              const double* part, const long long* vsum, int S, double* out, cudaStream_t st) {
     const long long rows = (long long)B * P.D;
-    k_ht_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part, out);
+    k_ht_combine<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(P, n, B, kernel, precision, tdh, part, vsum, S,
+                                                                   out);
     return cudaGetLastError();
 }
 

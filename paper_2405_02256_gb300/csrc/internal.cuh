@@ -72,6 +72,12 @@ struct ImgDesc {
     // evaluation kernels: 1 / (2 (m_k - 1)) in FP64 (0 for an axis of length 1), so that
     // per-direction weights take a multiply rather than an FP64 division
     double inv2m[kMaxDim];
+    // slab of a volume (3-D): the tables hold the vertices of planes [zlo, zlo + nz) of a
+    // volume of m_2 planes, whose pixels start at plane zbase (zlo - 1 or zlo) at `offset`.
+    // A whole image has zlo = zbase = 0, nz = m_2.
+    int zlo;
+    int zbase;
+    int nz;
 };
 
 // Device view of a tables handle.
