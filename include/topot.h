@@ -9,9 +9,11 @@
  *
  * Conventions shared by every call
  * --------------------------------
- * - An image with n in {2, 3} axes has lengths m_0 .. m_{n-1}, m_0 being the FASTEST
+ * - An image with n in {2, 3, 4} axes has lengths m_0 .. m_{n-1}, m_0 being the FASTEST
  *   memory axis; every m_k >= 2.  Vertex v = (i_0, .., i_{n-1}) has linear index
- *   i_0 + m_0 (i_1 + m_1 i_2).
+ *   i_0 + m_0 (i_1 + m_1 (i_2 + m_2 i_3)).  The method holds in any dimension (Section
+ *   2.1); n = 2 and 3 run on specialised kernels, n = 4 on plain generic-n kernels (same
+ *   calls, same results, slower).
  * - Complex: "dual"/vertex construction (Section 5): pixels are vertices, a cube
  *   exists iff all its vertices are pixels, and carries the minimum of their values.
  *   The top-dimensional construction (TOPOT_TOP) is described at topot_construction;
@@ -23,7 +25,8 @@
  *   are decided exactly as the FP64 expressions
  *       s   = fl(fl(fl(xi_0 x_0) + fl(xi_1 x_1)) + fl(xi_2 x_2))
  *       t_j = fl(a + fl(fl(j fl(b - a)) / (T - 1)))
- *   would decide them; integer results (tables, ECT, Radon) are therefore exact.
+ *   would decide them (the sum continuing left to right for n = 4); integer results
+ *   (tables, ECT, Radon) are therefore exact.
  * - Pointers named d_* are DEVICE pointers, h_* HOST pointers; the caller owns them.
  *   `stream` is a cudaStream_t (NULL = legacy default stream).  Unless stated
  *   otherwise calls only enqueue work on `stream` and return; outputs are valid once
@@ -110,8 +113,9 @@ typedef struct {
  *
  * d_pixels : image data (uint8 or int32, see dtype); image b starts at element
  *            h_offsets[b] and has h_shapes[b*n + k] = m_k.  Images must not alias
- *            outputs.  int32 values must satisfy |phi| < 2^26.
- * B        : number of images, >= 1.  n: 2 or 3.
+ *            outputs.  int32 values must satisfy |phi| < 2^26 (n = 4: 2^25).
+ * B        : number of images, >= 1.  n: 2, 3 or 4 (4: vertex construction only,
+ *            TOPOT_TOP gives UNSUPPORTED).
  * out      : receives a new handle; release it with free_tables().
  * Synchronous: allocates, launches the extraction on `stream`, waits for it and
  * reads the table sizes back.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA,

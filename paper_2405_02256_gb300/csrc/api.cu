@@ -13,6 +13,11 @@
 namespace topot {
 cudaError_t launch_extract(int n, topot_dtype dtype, bool top, const ExtractArgs& a, cudaStream_t st);
 cudaError_t launch_segment_sums(const TablesDev& t, long long* vsum, cudaStream_t st);
+int gen_block();
+cudaError_t launch_extract_gen(const TablesDev& t, topot_dtype dtype, const void* pixels, long long nblk,
+                               long long* cnt, cudaStream_t st);
+cudaError_t launch_hist_gen(const EvalPlan& P, const TablesDev& t, int32_t* lo, int32_t* hi, int grid,
+                            cudaStream_t st);
 cudaError_t launch_slab_sum_i32(const int32_t* parts, int P, long long n, int32_t* out, unsigned* err, int sm_count,
                                 cudaStream_t st);
 cudaError_t launch_slab_sum_f64(const double* parts, int P, long long n, double* out, int sm_count,
@@ -62,6 +67,7 @@ struct topot_tables {
     bool u8 = false;          // 8-bit batch, vertex construction: extraction by k_extract_u8
     int stage_bytes = 0;      // its staged bytes per tile (max over images)
     bool top = false;         // top-dimensional construction: corner image, then k_extract
+    bool gen = false;         // n = 4: the generic-n kernels (generic.cu) for every step
     void* top_buf = nullptr;  // TopSrc[B] followed by the int32 corner images
     TopSrc* d_top = nullptr;
     int32_t* d_corner = nullptr;
@@ -192,7 +198,9 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
     if (construction != TOPOT_VERTEX && construction != TOPOT_TOP)
         return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad construction");
     if (dtype != TOPOT_U8 && dtype != TOPOT_I32) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad dtype");
-    if (n != 2 && n != 3) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: n must be 2 or 3");
+    if (n < 2 || n > 4) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: n must be 2, 3 or 4");
+    if (n == 4 && construction == TOPOT_TOP)
+        return fail(TOPOT_ERR_UNSUPPORTED, "tables_create: the top-dimensional construction needs n <= 3");
     if (B < 1 || !h_shapes || !h_offsets) return fail(TOPOT_ERR_INVALID_ARG, "tables_create: bad image list");
 
     topot_tables* t = new (std::nothrow) topot_tables();
@@ -216,7 +224,8 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
     const int NP = n == 3 ? 3 : 1;
     const size_t smem_budget = 96 * 1024;
     t->top = top;
-    t->u8 = dtype == TOPOT_U8 && !top;
+    t->gen = n == 4;                      // generic-n kernels for every step
+    t->u8 = dtype == TOPOT_U8 && !top && !t->gen;
     std::vector<TopSrc> h_top(top ? B : 0);
     long long v_elems = 0;
     long long tiles = 0, entries = 0;
@@ -226,7 +235,7 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         ImgDesc& I = t->h_img[b];
         memset(&I, 0, sizeof(I));
         long long N = 1;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kMaxDim; ++k) {
             const long long pm = k < n ? h_shapes[(long long)b * n + k] : 1;
             // vertices per axis: the pixels (vertex construction) or the pixel corners (top)
             const long long m = (top && k < n) ? pm + 1 : pm;
@@ -237,7 +246,7 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
             }
             I.m[k] = (int)m;
             N *= m;
-            if (top) h_top[b].m[k] = (int)pm;
+            if (top && k < 3) h_top[b].m[k] = (int)pm;
         }
         if (N >= (1ll << 31) || h_offsets[b] < 0) {
             delete t;
@@ -273,6 +282,11 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         entries += N * t->S;
         I.tile_begin = tiles;
         const int m0 = I.m[0], m1 = I.m[1];
+        for (int k = 0; k < kMaxDim; ++k) I.inv2m[k] = I.m[k] > 1 ? 0.5 / (double)(I.m[k] - 1) : 0.0;
+        if (t->gen) {   // one block of gen_block() vertices per tile
+            tiles += (N + gen_block() - 1) / gen_block();
+            continue;
+        }
         if (t->u8) {
             // strips of `strip` vertices, one per thread; R full rows or one piece of a row
             const int strip = extract_u8_strip(n), threads = extract_u8_threads(n);
@@ -296,7 +310,6 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         I.segs_per_row = (m0 + I.W - 1) / I.W;
         I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
         tiles += (long long)I.tiles_per_plane * I.nz;
-        for (int k = 0; k < kMaxDim; ++k) I.inv2m[k] = I.m[k] > 1 ? 0.5 / (double)(I.m[k] - 1) : 0.0;
         I.div0 = make_fastdiv((uint32_t)m0);
         I.div1 = make_fastdiv((uint32_t)m1);
         I.div_spr = make_fastdiv((uint32_t)std::max(1, I.spr));
@@ -366,8 +379,9 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         free_tables(t);
         return cuda_fail(e, "tables_create: initialise metadata");
     }
-    const size_t smem = t->u8 ? extract_u8_smem_bytes(n, t->stage_bytes)
-                                  : extract_smem_bytes(n, elem, t->row_stride, t->stage_rows);
+    const size_t smem = t->gen ? 0
+                               : (t->u8 ? extract_u8_smem_bytes(n, t->stage_bytes)
+                                        : extract_smem_bytes(n, elem, t->row_stride, t->stage_rows));
     if (smem > 200 * 1024) {
         free_tables(t);
         return fail(TOPOT_ERR_UNSUPPORTED, "tables_create: rows too wide for the shared-memory stage");
@@ -403,7 +417,11 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     a.row_stride = t->row_stride;
     a.stage_rows = t->stage_rows;
     a.stage_bytes = t->stage_bytes;
-    if (t->top) {
+    if (t->gen) {
+        // per-block counts live in the look-back status words (tiles x S entries)
+        TOPOT_CUDA(launch_extract_gen(t->dev(), t->dtype, d_pixels, t->num_tiles,
+                                      reinterpret_cast<long long*>(t->status), st));
+    } else if (t->top) {
         TOPOT_CUDA(launch_top_prepass(d_pixels, t->dtype, t->d_corner, t->d_top, t->B, t->n, t->max_nv, t->sm_count,
                                       st));
         a.pixels = t->d_corner;
@@ -547,8 +565,8 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int nsets = per_image_dirs ? t->B : 1;
     const int NO = t->NO;
-    const int td = hist_tile(t, D, D / NO, T);
-    if (hist_smem_bytes(td, T) > 200 * 1024)
+    const int td = t->gen ? 32 : hist_tile(t, D, D / NO, T);
+    if (!t->gen && hist_smem_bytes(td, T) > 200 * 1024)
         return fail(TOPOT_ERR_UNSUPPORTED, std::string(name) + ": too many thresholds for the shared histogram");
     const int npairs = t->B * NO * (mode == kModeRadon ? 2 : 1);
     const size_t out_elems = (size_t)t->B * D * T;
@@ -587,7 +605,8 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     int per_sm = std::max(1, (int)((220 * 1024) / (hist_smem_bytes(td, T) + 1024)));
     per_sm = std::min(per_sm, 8);
     if (t->tuning.ect_ctas_per_sm > 0) per_sm = std::min(per_sm, t->tuning.ect_ctas_per_sm);
-    TOPOT_CUDA(launch_hist(P, t->dev(), td, d_out, hi, t->sm_count * per_sm, st));
+    if (t->gen) TOPOT_CUDA(launch_hist_gen(P, t->dev(), d_out, hi, t->sm_count * 8, st));
+    else TOPOT_CUDA(launch_hist(P, t->dev(), td, d_out, hi, t->sm_count * per_sm, st));
     TOPOT_CUDA(launch_hist_finish(mode, t->B, D, T, t->chi, d_out, hi, st));
     return TOPOT_OK;
 }
@@ -624,7 +643,7 @@ static HtSizing ht_sizing(const topot_tables* t, topot_kernel kernel, topot_prec
     HtSizing z;
     const int nsets = per_image_dirs ? t->B : 1;
     const int NO = t->NO;
-    if (precision == TOPOT_FP32C) {
+    if (precision == TOPOT_FP32C && !t->gen) {
         z.dl = t->tuning.ht_dirs_per_lane;
         const int per_orthant = D / NO;
         if (z.dl == 0) {

@@ -90,6 +90,26 @@ __device__ __forceinline__ void decode_item(const EvalPlan& P, long long item, i
     chunk = (int)(local - (long long)tile * nch);
 }
 
+// Tabulated kernel in FP64: the piecewise-linear interpolant of the samples (constant
+// outside [a, b]) and its slope (zero outside [a, b)), as kernel_table_create states them.
+__device__ __forceinline__ double table_kbar64(const EvalPlan& P, double s) {
+    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
+    const int K = P.ktab_k;
+    if (u < 0.0) return P.ktab64[0];
+    if (!(u < (double)(K - 1))) return P.ktab64[K - 1];
+    const double fi = floor(u);
+    const int i = (int)fi;
+    const double y0 = P.ktab64[i];
+    return __dadd_rn(y0, __dmul_rn(__dsub_rn(u, fi), __dsub_rn(P.ktab64[i + 1], y0)));
+}
+
+__device__ __forceinline__ double table_kappa64(const EvalPlan& P, double s) {
+    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
+    if (!(u >= 0.0 && u < (double)(P.ktab_k - 1))) return 0.0;
+    const int i = (int)floor(u);
+    return __ddiv_rn(__dsub_rn(P.ktab64[i + 1], P.ktab64[i]), P.ktab_h);
+}
+
 cudaError_t launch_dir_prep(const EvalPlan& P, int n, cudaStream_t st);
 cudaError_t launch_plan(const EvalPlan& P, const TablesDev& t, cudaStream_t st);
 

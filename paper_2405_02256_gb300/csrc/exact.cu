@@ -73,21 +73,31 @@ __global__ void __launch_bounds__(256) k_exact_keys(ExactArgs a) {
         int* V = a.val[0] + (long long)seg * a.cap;
         const int* ai = T.arena_idx + base;
         const Tval* av = reinterpret_cast<const Tval*>(T.arena_val) + base;
-        const int m0 = I.m[0], m1 = I.m[1], m2 = I.m[2];
+        const int m0 = I.m[0], m1 = I.m[1], m2 = I.m[2], m3 = I.m[3];
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x) {
             const uint32_t idx = (uint32_t)ai[i];
-            int c[3];
-            const uint32_t q1 = fastdiv(idx, I.div0);
-            c[0] = (int)(idx - q1 * (uint32_t)m0);
-            if (NDIM == 2) {
-                c[1] = (int)q1;
+            int c[4];
+            if (NDIM == 4) {   // generic-n tables: plain division
+                uint32_t r = idx;
+                c[0] = (int)(r % (uint32_t)m0);
+                r /= (uint32_t)m0;
+                c[1] = (int)(r % (uint32_t)m1);
+                r /= (uint32_t)m1;
+                c[2] = (int)(r % (uint32_t)m2);
+                c[3] = (int)(r / (uint32_t)m2);
             } else {
-                const uint32_t q2 = fastdiv(q1, I.div1);
-                c[1] = (int)(q1 - q2 * (uint32_t)m1);
-                c[2] = (int)q2;
+                const uint32_t q1 = fastdiv(idx, I.div0);
+                c[0] = (int)(idx - q1 * (uint32_t)m0);
+                if (NDIM == 2) {
+                    c[1] = (int)q1;
+                } else {
+                    const uint32_t q2 = fastdiv(q1, I.div1);
+                    c[1] = (int)(q1 - q2 * (uint32_t)m1);
+                    c[2] = (int)q2;
+                }
             }
-            const int mm[3] = {m0, m1, m2};
+            const int mm[4] = {m0, m1, m2, m3};
             double s = 0.0;
 #pragma unroll
             for (int k = 0; k < NDIM; ++k) {
@@ -320,9 +330,12 @@ cudaError_t launch_exact(int n, bool u8, ExactArgs a, long long max_n, int sm_co
     if (n == 2) {
         if (u8) k_exact_keys<2, int16_t><<<gk, 256, 0, st>>>(a);
         else k_exact_keys<2, int32_t><<<gk, 256, 0, st>>>(a);
-    } else {
+    } else if (n == 3) {
         if (u8) k_exact_keys<3, int16_t><<<gk, 256, 0, st>>>(a);
         else k_exact_keys<3, int32_t><<<gk, 256, 0, st>>>(a);
+    } else {
+        if (u8) k_exact_keys<4, int16_t><<<gk, 256, 0, st>>>(a);
+        else k_exact_keys<4, int32_t><<<gk, 256, 0, st>>>(a);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

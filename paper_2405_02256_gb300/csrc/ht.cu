@@ -683,24 +683,6 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
 // [a, b]; kappa is its derivative, the segment slope on [a + i h, a + (i + 1) h) and zero
 // outside [a, b).
 
-__device__ __forceinline__ double table_kbar64(const EvalPlan& P, double s) {
-    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
-    const int K = P.ktab_k;
-    if (u < 0.0) return P.ktab64[0];
-    if (!(u < (double)(K - 1))) return P.ktab64[K - 1];
-    const double fi = floor(u);
-    const int i = (int)fi;
-    const double y0 = P.ktab64[i];
-    return __dadd_rn(y0, __dmul_rn(__dsub_rn(u, fi), __dsub_rn(P.ktab64[i + 1], y0)));
-}
-
-__device__ __forceinline__ double table_kappa64(const EvalPlan& P, double s) {
-    const double u = __ddiv_rn(__dsub_rn(s, P.ktab_a), P.ktab_h);
-    if (!(u >= 0.0 && u < (double)(P.ktab_k - 1))) return 0.0;
-    const int i = (int)floor(u);
-    return __ddiv_rn(__dsub_rn(P.ktab64[i + 1], P.ktab64[i]), P.ktab_h);
-}
-
 // FP32: the position p = u + 1/2 is clamped to [0, K] by a saturating FMA on the scaled
 // position p / K, and rounded to the nearest integer j by one FMA that adds 1.5 * 2^23
 // (j lands in the low mantissa bits: no conversion instruction).  The padded table holds
@@ -1351,10 +1333,10 @@ __global__ void k_ht_adj_combine(EvalPlan P, int n, int B, int kernel, int preci
         M *= 0.5;
         scale = M <= kLaplaceMaxM ? scale * exp(M) : __longlong_as_double(0x7ff8000000000000ll);
     }
-    double g[3] = {0.0, 0.0, 0.0};
+    double g[kMaxDim] = {0.0, 0.0, 0.0, 0.0};
     const int b0 = P.nsets == 1 ? 0 : set, b1 = P.nsets == 1 ? B : set + 1;
     for (int b = b0; b < b1; ++b) {
-        double v[6];
+        double v[2 * kMaxDim];
         gather_partials(P, NO, tdh, nc, b, d, o, part, v);
         const double* go = gout + ((long long)b * P.D + d) * nk;
         for (int k = 0; k < n; ++k) {
@@ -1463,8 +1445,12 @@ static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel
     }
 }
 
+cudaError_t launch_ht_gen(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int grid,
+                          double* part, cudaStream_t st);
+
 cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
                       int grid, double* part, cudaStream_t st) {
+    if (t.n == 4) return launch_ht_gen(P, t, kernel, precision, adjoint, grid, part, st);   // dl = 1
     if (t.n == 2) {
         if (t.val_bytes == 2) return launch_ht_n<2, int16_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
         return launch_ht_n<2, int32_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);

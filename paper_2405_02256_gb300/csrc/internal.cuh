@@ -8,7 +8,7 @@
 
 namespace topot {
 
-constexpr int kMaxDim = 3;
+constexpr int kMaxDim = 4;   // 2-D and 3-D specialised kernels; 4-D on the generic path
 
 // Device error word bits (OR-ed by kernels, read and cleared by tables_sync).
 enum DevErr : unsigned {
@@ -55,7 +55,7 @@ struct ImgDesc {
     long long N;            // vertices
     long long seg_base;     // arena entry offset of segment 0 (segments are N apart)
     long long tile_begin;   // first extraction tile (global numbering)
-    int m[kMaxDim];         // axis lengths, m_0 fastest; m_2 = 1 for n = 2
+    int m[kMaxDim];         // axis lengths, m_0 fastest; 1 beyond n
     int W;                  // extraction tile width (columns)
     int R;                  // extraction tile rows (1 when W < m_0)
     int segs_per_row;       // ceil(m_0 / W)

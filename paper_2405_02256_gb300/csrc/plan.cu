@@ -67,21 +67,21 @@ __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
 // (ties by direction id), so that a tile of 32 DL consecutive directions spans a narrow
 // range of |<xi, v>| and its polynomial degree (chosen per tile from the largest M) stays
 // low.  One block per direction set sorts the keys
-//   orthant (3 bits) | FP32 bits of M (order-preserving for M >= 0) | direction id (29 bits)
+//   orthant (4 bits) | FP32 bits of M (order-preserving for M >= 0) | direction id (28 bits)
 // with a bitonic network in shared memory; sets of more than kSortDirsMax directions keep
 // the plain orthant grouping.
 constexpr int kSortDirsMax = 8192;
 
 __global__ void __launch_bounds__(1024) k_dir_sort(EvalPlan P, int n) {
     extern __shared__ unsigned long long key[];
-    __shared__ int cnt[8];
+    __shared__ int cnt[16];
     const int set = blockIdx.x;
     const int tid = threadIdx.x;
     const int NO = 1 << n;
     const double* dirs = P.dirs + (long long)set * P.D * n;
     int L = 1;
     while (L < P.D) L <<= 1;
-    if (tid < 8) cnt[tid] = 0;
+    if (tid < 16) cnt[tid] = 0;
     __syncthreads();
     for (int d = tid; d < L; d += 1024) {
         unsigned long long k = ~0ull;   // padding sorts last
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_dir_sort(EvalPlan P, int n) {
             for (int c = 0; c < n; ++c) m += fabs(xi[c]);
             const int o = orthant_of(xi, n);
             atomicAdd(&cnt[o], 1);
-            k = ((unsigned long long)o << 61) | ((unsigned long long)__float_as_uint((float)m) << 29) |
+            k = ((unsigned long long)o << 60) | ((unsigned long long)__float_as_uint((float)m) << 28) |
                 (unsigned long long)d;
         }
         key[d] = k;
@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(1024) k_dir_sort(EvalPlan P, int n) {
     int* perm = P.perm + (long long)set * P.D;
     for (int i = tid; i < P.D; i += 1024) {
         const unsigned long long k = key[i];
-        const int d = (int)(k & ((1ull << 29) - 1));
-        const int o = (int)(k >> 61);
+        const int d = (int)(k & ((1ull << 28) - 1));
+        const int o = (int)(k >> 60);
         perm[i] = d;
         P.rank[(long long)set * P.D + d] = i - bo[o];
     }
@@ -143,7 +143,8 @@ cudaError_t launch_dir_prep(const EvalPlan& P, int n, cudaStream_t st) {
         return cudaGetLastError();
     }
     if (n == 2) k_dir_prep<4><<<P.nsets, 1024, 0, st>>>(P, n);
-    else k_dir_prep<8><<<P.nsets, 1024, 0, st>>>(P, n);
+    else if (n == 3) k_dir_prep<8><<<P.nsets, 1024, 0, st>>>(P, n);
+    else k_dir_prep<16><<<P.nsets, 1024, 0, st>>>(P, n);
     return cudaGetLastError();
 }
 

@@ -46,9 +46,16 @@ def test_last_error_without_gpu(lib_path):
     h = ctypes.c_void_p()
     shapes = (ctypes.c_int64 * 2)(4, 4)
     offs = (ctypes.c_int64 * 1)(0)
-    # n = 4 is rejected before any CUDA call
-    st = L.tables_create(0, 4, shapes, offs, 1, 0, ctypes.byref(h))
-    assert st == 1 and b"n must be 2 or 3" in L.topot_last_error()
+    # n = 5 is rejected before any CUDA call, and so are the top construction in 4-D and
+    # slabs of anything but 3-D volumes
+    st = L.tables_create(0, 5, shapes, offs, 1, 0, ctypes.byref(h))
+    assert st == 1 and b"n must be 2, 3 or 4" in L.topot_last_error()
+    st = L.tables_create(0, 4, shapes, offs, 1, 1, ctypes.byref(h))
+    assert st == 2 and b"top-dimensional" in L.topot_last_error()
+    zr = (ctypes.c_int64 * 2)(0, 2)
+    st = L.tables_create_slab(0, 2, shapes, offs, zr, 1, ctypes.byref(h))
+    assert st == 2 and b"slabs of 3-D volumes" in L.topot_last_error()
+    assert L.slab_sum_f64(None, 1, 1, None, None) == 1
     st = L.tables_create(0, 2, shapes, offs, 1, 7, ctypes.byref(h))
     assert st == 1 and b"construction" in L.topot_last_error()
 

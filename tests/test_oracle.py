@@ -121,6 +121,10 @@ def _tiny_images():
         rng = np.random.default_rng(200 + seed)
         out.append(rng.integers(0, 5, size=shape).astype(np.int64))
     out.append(np.array([[3, -2, 7], [0, 5, -1]], dtype=np.int64))   # negative values
+    # n = 4 (the method holds in any dimension; the library's generic-n path)
+    for seed, shape in enumerate([(2, 3, 2, 3), (3, 2, 2, 2), (2, 2, 2, 2)]):
+        out.append(synth.bernoulli(shape, 0.5, seed=300 + seed))
+        out.append(np.random.default_rng(400 + seed).integers(-3, 4, size=shape).astype(np.int64))
     return out
 
 
