@@ -12,11 +12,15 @@ from paper_2405_02256_gb300 import synth
 
 
 def test_cpu_baseline_on_a_small_image():
+    """Two spawned processes on a small image: the keys the bench reports."""
     img = synth.grf((40, 48), 4.0, seed=3)
     dirs = synth.random_2d_dirs(16, 2, 0.01, 1.0)
-    out = bench.cpu_baseline(img, dirs, budget_s=0.2)
-    assert out["kind"] == "oracle" and out["cores"] == 1 and out["unit"] == bench.UNIT
+    out = bench.cpu_baseline(img, synth.circle_dirs(8), dirs, budget_s=0.3, procs=2)
+    assert out["kind"] == "oracle" and out["cores"] == 2 and out["nproc"] >= 1 and out["unit"] == bench.UNIT
     assert out["value"] > 0 and "40x48" in out["sample"]
+    for key in ("ect_dirs_per_s", "radon_dirs_per_s", "tables_s_per_image"):
+        assert out[key] > 0 and out["one_thread"][key] > 0
+    assert out["one_thread"]["value"] > 0
     # the counted terms are the Delta-table sizes of the directions' orthants
     tab = O.critical_tables(img)
     assert all(len(tab.delta_idx[r]) > 0 for r in range(2))
@@ -25,8 +29,8 @@ def test_cpu_baseline_on_a_small_image():
 def test_reference_arm_line(monkeypatch, capsys):
     monkeypatch.setattr(bench, "make_images", lambda count, side: [synth.grf((32, 32), 4.0, seed=1)])
     monkeypatch.setattr(bench, "cpu_baseline",
-                        lambda img, dirs, budget_s=0.0: {"value": 123.0, "unit": bench.UNIT, "cores": 1,
-                                                          "kind": "oracle", "sample": "stub"})
+                        lambda img, dirs_e, dirs_h, budget_s=0.0: {"value": 123.0, "unit": bench.UNIT, "cores": 1,
+                                                                   "kind": "oracle", "sample": "stub"})
     args = argparse.Namespace(images=64, side=2048, steps=2, warmup=3)
     bench.run_reference(args)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])

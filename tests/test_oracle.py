@@ -481,3 +481,22 @@ def test_table_gradient_central_differences():
             fp, _ = O.hybrid_transform(tab, kt, [xi + e])
             fm, _ = O.hybrid_transform(tab, kt, [xi - e])
             assert abs((fp[0] - fm[0]) / (2 * h) - g[di, k]) < 1e-5 * max(1.0, abs(g[di, k]))
+
+
+# ---------------------------------------------------------------- the oracle over processes
+
+@pytest.mark.parametrize("parts", [1, 3, 7])
+def test_row_block_tables_equal_whole_image(parts):
+    """The CPU baseline's split of the tables over vertices (row blocks with a one-row halo)
+    gives the whole image's tables, entry for entry."""
+    from oracle import parallel as OP
+    img = synth.grf((37, 29), 4.0, seed=77)
+    ref = O.critical_tables(img)
+    t = OP.merge_blocks(img.shape, [OP.block_tables(a) for a in OP.row_blocks(img, parts)])
+    for o in range(4):
+        np.testing.assert_array_equal(t.lower_idx[o], ref.lower_idx[o])
+        np.testing.assert_array_equal(t.lower_val[o], ref.lower_val[o])
+    for r in range(2):
+        np.testing.assert_array_equal(t.delta_idx[r], ref.delta_idx[r])
+        np.testing.assert_array_equal(t.delta_val[r], ref.delta_val[r])
+    assert t.chi == ref.chi
