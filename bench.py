@@ -465,6 +465,29 @@ def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_
     return rows
 
 
+def ragged_workload():
+    """BASELINE configuration 4: 10,000 grey images, sides log-uniform in [28, 512] (non-square),
+    uniform noise blurred by sigma = 2 px; ECT directions (64 on the circle) and Laplace
+    directions (256 unit vectors, uniform angle) shared by every image."""
+    from paper_2405_02256_gb300 import synth
+    shapes = synth.ragged_shapes(10000, 28, 512, seed=4)
+    imgs = [synth.blurred_noise(s, 2.0, seed=400000 + i) for i, s in enumerate(shapes)]
+    return imgs, synth.circle_dirs(64), synth.random_2d_dirs(256, 44, 1.0, 1.0)
+
+
+def ragged_pipeline(tb, batch, ect_h, ht_h, dev):
+    """The graph the bench times: extraction, ECT 64 x 64 and Laplace FP32C, tuned tiles."""
+    import torch
+
+    from paper_2405_02256_gb300 import synth
+    R2 = synth.image_radius(2)
+    pipe = tb.Pipeline(batch.shapes, batch.offsets, batch.pixels.numel(),
+                       ect=(torch.from_numpy(ect_h).to(dev), -R2, R2, 64),
+                       hybrid=[("laplace", torch.from_numpy(ht_h).to(dev), "fp32c")], tune=True)
+    pipe.pixels.copy_(batch.pixels)
+    return pipe.capture()
+
+
 def extra_workloads(dev):
     """BASELINE configurations 3-5: 3-D volumes, ragged batch under a CUDA graph, gradients."""
     import torch
@@ -473,20 +496,13 @@ def extra_workloads(dev):
     from paper_2405_02256_gb300 import synth
     rows = {}
 
-    # configuration 4: 10,000 ragged grey images, one CUDA graph per step
+    # configuration 4: 10,000 ragged grey images, one CUDA graph per step (tuned tiles)
     t0 = time.time()
-    shapes = synth.ragged_shapes(10000, 28, 512, seed=4)
-    imgs = [synth.blurred_noise(s, 2.0, seed=400000 + i) for i, s in enumerate(shapes)]
+    imgs, ect_h, ht_h = ragged_workload()
     gen_s = time.time() - t0
     batch = tb.pack_images(imgs, device=dev)
     R2 = synth.image_radius(2)
-    ect_h = synth.circle_dirs(64)
-    ht_h = synth.random_2d_dirs(256, 44, 1.0, 1.0)
-    pipe = tb.Pipeline(batch.shapes, batch.offsets, batch.pixels.numel(),
-                       ect=(torch.from_numpy(ect_h).to(dev), -R2, R2, 64),
-                       hybrid=[("laplace", torch.from_numpy(ht_h).to(dev), "fp32c")])
-    pipe.pixels.copy_(batch.pixels)
-    pipe.capture()
+    pipe = ragged_pipeline(tb, batch, ect_h, ht_h, dev)
     ms = _time_cuda(lambda: pipe.run(), reps=5)
     # the three parts of the step, each launched on its own (outside the graph)
     ect_d = torch.from_numpy(ect_h).to(dev)
@@ -506,7 +522,10 @@ def extra_workloads(dev):
                     "Laplace at 256 unit dirs per image; extraction + ECT + Laplace replayed as one CUDA graph",
         "ms_per_step": ms, "images_per_s": len(imgs) / (ms / 1e3), "pixels": px,
         "ect_dirs_per_s": len(imgs) * 64 / (ms / 1e3), "laplace_terms_per_s_whole_step": terms / (ms / 1e3),
-        "parts": ms_parts, "input_gen_s": gen_s}
+        "laplace_terms_per_s": terms / (ms_parts["laplace_ms"] / 1e3),
+        "ect_updates_per_s": int((nl * np.bincount(_orthants(ect_h), minlength=4)[None, :]).sum())
+                             / (ms_parts["ect_ms"] / 1e3),
+        "tuned_tiles": pipe.tuned, "parts": ms_parts, "input_gen_s": gen_s}
     pipe.tables.free()
     del pipe, batch, imgs
 

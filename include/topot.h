@@ -30,8 +30,11 @@
  * - Pointers named d_* are DEVICE pointers, h_* HOST pointers; the caller owns them.
  *   `stream` is a cudaStream_t (NULL = legacy default stream).  Unless stated
  *   otherwise calls only enqueue work on `stream` and return; outputs are valid once
- *   the stream has reached that point.  Calls that use one tables handle must be
- *   ordered on one stream (the handle owns a single workspace).
+ *   the stream has reached that point.  A handle owns one workspace per family of
+ *   calls: (ect, radon), (hybrid transforms and gradients, tabulated or not),
+ *   (exact_representation).  Calls of one family on one handle must be ordered on one
+ *   stream; calls of different families may run concurrently once the tables are built,
+ *   and tables_build must be ordered with all of them.
  * - No exception crosses the ABI.  Every call returns a topot_status; on error the
  *   outputs are unspecified and topot_last_error() gives a message (thread-local).
  * - Directions must be finite.
@@ -97,6 +100,9 @@ typedef struct {
     int ht_dirs_per_lane;     /* hybrid FP32C: 1, 2, 4 (8: Laplace) directions per lane    */
     int ht_chunk;             /* hybrid: critical points per work item (x256)             */
     int ht_ctas_per_sm;       /* hybrid: resident blocks per SM of the persistent grid     */
+    int ht_warp_split;        /* hybrid FP32C forward: 1 or 2 point groups per warp; with 2
+                                 (and 2 or 4 directions per lane) a tile has 16 x directions
+                                 per lane, for small direction sets                        */
 } topot_tuning;
 
 /* ---------------------------------------------------------------------------

@@ -22,8 +22,9 @@ CACHE = os.environ.get("TOPOT_TUNE_CACHE",
 
 ECT_SPACE = [dict(ect_dirs_per_warp=td, ect_chunk=ch, ect_ctas_per_sm=c)
              for td in (8, 16, 32, 64) for ch in (0, 16384, 131072) for c in (0, 1)]
-HT_SPACE = [dict(ht_dirs_per_lane=dl, ht_chunk=ch, ht_ctas_per_sm=c)
-            for dl in (1, 2, 4, 8) for ch in (0, 16384, 131072) for c in (0, 3)]
+HT_SPACE = [dict(ht_dirs_per_lane=dl, ht_chunk=ch, ht_ctas_per_sm=c, ht_warp_split=sp)
+            for dl in (1, 2, 4, 8) for ch in (0, 16384, 131072) for c in (0, 3) for sp in (1, 2)
+            if sp == 1 or dl in (2, 4)]
 
 
 def _load_cache() -> dict:

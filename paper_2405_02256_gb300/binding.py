@@ -41,7 +41,8 @@ class TopotError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("ect_dirs_per_warp", ctypes.c_int), ("ect_chunk", ctypes.c_int), ("ect_ctas_per_sm", ctypes.c_int),
-                ("ht_dirs_per_lane", ctypes.c_int), ("ht_chunk", ctypes.c_int), ("ht_ctas_per_sm", ctypes.c_int)]
+                ("ht_dirs_per_lane", ctypes.c_int), ("ht_chunk", ctypes.c_int), ("ht_ctas_per_sm", ctypes.c_int),
+                ("ht_warp_split", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -472,11 +473,15 @@ class Pipeline:
 
     The tables handle, the pixel buffer and every output are allocated once; ``run``
     copies new pixels into the captured input buffer and replays the graph (no host
-    synchronisation, no allocation, every kernel of the path in one graph launch).
+    synchronisation, no allocation, every kernel of the path in one graph launch).  In
+    the graph the grid transforms (ECT, Radon) run on a second stream beside the hybrid
+    transforms: the handle gives each family of calls its own workspace.  With
+    ``tune=True``, ``capture`` first picks the tile shapes of every operation with the
+    autotuner (cached per GPU and size, see autotune.py).
     """
 
     def __init__(self, shapes, offsets, n_pixels: int, dtype=U8, ect=None, radon=None, hybrid=(),
-                 device="cuda"):
+                 device="cuda", tune: bool = False):
         """ect / radon: (dirs, t_min, t_max, T) or None; hybrid: list of (kernel, dirs, precision)."""
         self.tables = tables_create(shapes, offsets, dtype)
         tdt = torch.uint8 if dtype == U8 else torch.int32
@@ -493,23 +498,56 @@ class Pipeline:
             shape = (B, D, 2) if kernel == "fourier" else (B, D)
             self.hybrid_out.append(torch.empty(shape, dtype=torch.float64, device=device))
         self.graph = None
+        self.tune = tune
+        self.tuned = {}
+        self.side = torch.cuda.Stream(device=device)
 
-    def _launch(self):
-        self.tables.build(self.pixels)
+    def _grid(self):
         if self.ect_args is not None:
             d, a, b, T = self.ect_args
             ect(self.tables, d, a, b, T, out=self.ect_out)
         if self.radon_args is not None:
             d, a, b, T = self.radon_args
             radon(self.tables, d, a, b, T, out=self.radon_out)
+
+    def _hybrid(self):
         for (kernel, d, prec), out in zip(self.hybrid_args, self.hybrid_out):
             hybrid_transform(self.tables, kernel, d, prec, out=out)
 
+    def _launch(self):
+        self.tables.build(self.pixels)
+        if (self.ect_args is not None or self.radon_args is not None) and self.hybrid_args:
+            main = torch.cuda.current_stream()
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                self._grid()
+            self._hybrid()
+            main.wait_stream(self.side)
+        else:
+            self._grid()
+            self._hybrid()
+
+    def _autotune(self):
+        from . import autotune
+        if self.ect_args is not None:
+            d, a, b, T = self.ect_args
+            self.tuned["ect"] = autotune.tune(self.tables, "ect", d, t_min=a, t_max=b, T=T)["tuning"]
+        if self.radon_args is not None:
+            d, a, b, T = self.radon_args
+            self.tuned["radon"] = autotune.tune(self.tables, "radon", d, t_min=a, t_max=b, T=T)["tuning"]
+        for kernel, d, prec in self.hybrid_args:   # one tiling per handle: the last kernel's wins
+            self.tuned[kernel] = autotune.tune(self.tables, "hybrid", d, kernel=kernel, precision=prec)["tuning"]
+
     def capture(self):
-        """Run once eagerly (sizes every workspace), then capture the launch sequence."""
+        """Run once eagerly (sizes every workspace; tunes the tiles when asked), then capture
+        the launch sequence."""
         self._launch()
         torch.cuda.synchronize()
         self.tables.sync()
+        if self.tune:
+            self._autotune()
+            self._launch()   # the workspaces of the chosen tiles
+            torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             self._launch()

@@ -39,7 +39,7 @@ cudaError_t launch_hist(const EvalPlan& P, const TablesDev& t, int td, int32_t* 
 cudaError_t launch_hist_finish(int mode, int B, int D, int T, const long long* chi, int32_t* out,
                                const int32_t* hi, cudaStream_t st);
 cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
-                      int grid, double* part, cudaStream_t st);
+                      int split, int grid, double* part, cudaStream_t st);
 cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
                               const double* part, const long long* vsum, int S, double* out, cudaStream_t st);
 cudaError_t launch_ht_adj_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,
@@ -89,9 +89,10 @@ struct topot_tables {
     // host copies (valid after tables_sync)
     bool host_valid = false;
     std::vector<long long> h_seg_count, h_chi, h_absum;
-    // evaluation workspace, grown on demand
-    void* ws = nullptr;
-    size_t ws_bytes = 0;
+    // evaluation workspaces, grown on demand, one per family of calls (grid transforms,
+    // hybrid transforms, exact representations), so that families can run concurrently
+    void* ws[3] = {nullptr, nullptr, nullptr};
+    size_t ws_bytes[3] = {0, 0, 0};
     topot_tuning tuning{};
 
     TablesDev dev() const {
@@ -133,18 +134,20 @@ topot_status cuda_fail(cudaError_t e, const char* where) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-topot_status ensure_ws(topot_tables* t, size_t bytes) {
-    if (t->ws_bytes >= bytes) return TOPOT_OK;
-    if (t->ws) {
-        cudaError_t e = cudaFree(t->ws);
-        t->ws = nullptr;
-        t->ws_bytes = 0;
+enum WsFamily : int { kWsGrid = 0, kWsHybrid = 1, kWsExact = 2, kWsFamilies = 3 };
+
+topot_status ensure_ws(topot_tables* t, int fam, size_t bytes) {
+    if (t->ws_bytes[fam] >= bytes) return TOPOT_OK;
+    if (t->ws[fam]) {
+        cudaError_t e = cudaFree(t->ws[fam]);
+        t->ws[fam] = nullptr;
+        t->ws_bytes[fam] = 0;
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
     }
     const size_t sz = align_up(bytes + bytes / 4, 1 << 20);
-    cudaError_t e = cudaMalloc(&t->ws, sz);
+    cudaError_t e = cudaMalloc(&t->ws[fam], sz);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
-    t->ws_bytes = sz;
+    t->ws_bytes[fam] = sz;
     return TOPOT_OK;
 }
 
@@ -530,7 +533,8 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
         (u.ht_dirs_per_lane && u.ht_dirs_per_lane != 1 && u.ht_dirs_per_lane != 2 && u.ht_dirs_per_lane != 4 &&
          u.ht_dirs_per_lane != 8) ||
         u.ect_chunk < 0 || (u.ect_chunk % 256) != 0 || u.ht_chunk < 0 || (u.ht_chunk % 256) != 0 ||
-        u.ect_ctas_per_sm < 0 || u.ect_ctas_per_sm > 32 || u.ht_ctas_per_sm < 0 || u.ht_ctas_per_sm > 32)
+        u.ect_ctas_per_sm < 0 || u.ect_ctas_per_sm > 32 || u.ht_ctas_per_sm < 0 || u.ht_ctas_per_sm > 32 ||
+        (u.ht_warp_split != 0 && u.ht_warp_split != 1 && u.ht_warp_split != 2))
         return fail(TOPOT_ERR_INVALID_ARG, "tables_set_tuning: value out of range");
     t->tuning = u;
     return TOPOT_OK;
@@ -538,12 +542,25 @@ topot_status tables_set_tuning(topot_tables* t, const topot_tuning* tuning) {
 
 void free_tables(topot_tables* t) {
     if (!t) return;
-    if (t->ws) cudaFree(t->ws);
+    for (int f = 0; f < kWsFamilies; ++f)
+        if (t->ws[f]) cudaFree(t->ws[f]);
     if (t->top_buf) cudaFree(t->top_buf);
     if (t->arena_val) cudaFree(t->arena_val);
     if (t->arena_idx) cudaFree(t->arena_idx);
     if (t->meta) cudaFree(t->meta);
     delete t;
+}
+
+// Bound on the work items of a plan: with automatic chunking the planner aims at `target`
+// items of balanced size, plus at most one partial chunk per (pair, tile), and every
+// direction set has at most D / tile + 2^n tiles over its orthants; with a requested
+// chunk, every (tile, chunk) of every image.  `parts`: pairs per (image, orthant).
+static long long plan_max_items(const topot_tables* t, int D, int tile, int chunk_req, int parts, int target) {
+    const long long tiles = (D + tile - 1) / tile + t->NO;
+    if (chunk_req <= 0) return target + (long long)t->B * tiles * parts;
+    long long m = 0;
+    for (int b = 0; b < t->B; ++b) m += tiles * ((t->h_img[b].N + chunk_req - 1) / chunk_req) * parts;
+    return m;
 }
 
 // ---- grid transforms ---------------------------------------------------------------------------
@@ -570,12 +587,15 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
         return fail(TOPOT_ERR_UNSUPPORTED, std::string(name) + ": too many thresholds for the shared histogram");
     const int npairs = t->B * NO * (mode == kModeRadon ? 2 : 1);
     const size_t out_elems = (size_t)t->B * D * T;
+    const long long max_items =
+        plan_max_items(t, D, td, t->tuning.ect_chunk, mode == kModeRadon ? 2 : 1, t->sm_count * 16);
     const size_t need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
                         sizeof(long long) * (npairs + 1) + sizeof(int) * npairs + sizeof(double) * T +
-                        (mode == kModeRadon ? sizeof(int32_t) * out_elems : 0) + 8 * 256;
-    topot_status s = ensure_ws(t, need);
+                        sizeof(int) * (size_t)max_items +
+                        (mode == kModeRadon ? sizeof(int32_t) * out_elems : 0) + 9 * 256;
+    topot_status s = ensure_ws(t, kWsGrid, need);
     if (s != TOPOT_OK) return s;
-    Carver cv{reinterpret_cast<char*>(t->ws)};
+    Carver cv{reinterpret_cast<char*>(t->ws[kWsGrid])};
     EvalPlan P{};
     P.mode = mode;
     P.nsets = nsets;
@@ -584,15 +604,16 @@ static topot_status grid_transform(const char* name, int mode, const topot_table
     P.chunk_req = t->tuning.ect_chunk;
     P.target_items = t->sm_count * 16;
     P.npairs = npairs;
-    P.max_items = 1ll << 40;
+    P.max_items = max_items;
     P.dirs = d_dirs;
-    P.ctl = cv.take<int>(4);
+    P.ctl = cv.take<int>(8);
     P.perm = cv.take<int>((size_t)nsets * D);
     P.rank = cv.take<int>((size_t)nsets * D);
     P.boff = cv.take<int>((size_t)nsets * (NO + 1));
     P.pair_items = cv.take<long long>(npairs + 1);
     P.pair_chunks = cv.take<int>(npairs);
     P.thr = cv.take<double>(T);
+    P.item_pair = cv.take<int>((size_t)max_items);
     P.T = T;
     P.t_min = t_min;
     P.t_max = t_max;
@@ -629,6 +650,7 @@ topot_status radon(const topot_tables* t, const double* d_dirs, int D, int per_i
 // the same result for the same call.
 struct HtSizing {
     int dl = 1;               // directions per lane
+    int split = 1;            // point groups per warp (FP32C forward)
     int tdh = 32;             // directions per tile
     int ncomp = 1;            // FP64 partials per direction and item
     int npairs = 0;
@@ -645,31 +667,31 @@ static HtSizing ht_sizing(const topot_tables* t, topot_kernel kernel, topot_prec
     const int NO = t->NO;
     if (precision == TOPOT_FP32C && !t->gen) {
         z.dl = t->tuning.ht_dirs_per_lane;
+        z.split = t->tuning.ht_warp_split;
         const int per_orthant = D / NO;
         if (z.dl == 0) {
-            z.dl = per_orthant >= 128 ? 4 : (per_orthant >= 64 ? 2 : 1);
+            // a tile of 32 dl / split directions: fill it; with fewer than 128 directions per
+            // orthant two point groups per warp keep two or four directions per lane
+            z.dl = per_orthant >= 64 ? 4 : (per_orthant >= 32 ? 2 : 1);
+            if (z.split == 0) z.split = (per_orthant >= 32 && per_orthant < 128) ? 2 : 1;
             if (kernel == TOPOT_LAPLACE && per_orthant >= 256) z.dl = 8;
         }
         if (z.dl == 8 && kernel != TOPOT_LAPLACE) z.dl = 4;
+        if (z.split == 0 || z.dl == 1 || z.dl == 8 || adjoint || kernel == TOPOT_TABLE) z.split = 1;
         // adjoint: two direction pairs per lane for the one-component kernels in 2-D, else one
         if (adjoint && kernel != TOPOT_TABLE)
             z.dl = std::min(z.dl, (kernel != TOPOT_FOURIER && t->n == 2) ? 4 : 2);
     }
-    z.tdh = 32 * z.dl;
+    z.tdh = 32 * z.dl / z.split;
     const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
     z.ncomp = adjoint ? nk * t->n : nk;
     z.npairs = t->B * NO;
     z.target = t->sm_count * 16;
-    if (t->tuning.ht_chunk > 0) {
-        for (int b = 0; b < t->B; ++b)
-            z.max_items += (long long)((D + z.tdh - 1) / z.tdh + NO) *
-                           ((t->h_img[b].N + t->tuning.ht_chunk - 1) / t->tuning.ht_chunk);
-    } else {
-        z.max_items = z.target + (long long)t->B * ((D + z.tdh - 1) / z.tdh + NO);
-    }
+    z.max_items = plan_max_items(t, D, z.tdh, t->tuning.ht_chunk, 1, z.target);
     z.part_elems = (size_t)z.max_items * z.tdh * z.ncomp;
     z.need = 4096 + sizeof(int) * (size_t)nsets * D * 2 + sizeof(int) * (size_t)nsets * (NO + 1) +
-             sizeof(long long) * (z.npairs + 1) + sizeof(int) * z.npairs + sizeof(double) * z.part_elems + 8 * 256;
+             sizeof(long long) * (z.npairs + 1) + sizeof(int) * z.npairs + sizeof(double) * z.part_elems +
+             2 * sizeof(int) * (size_t)z.max_items + 10 * 256;
     return z;
 }
 
@@ -689,7 +711,7 @@ static EvalPlan ht_carve(const topot_tables* t, const HtSizing& z, const double*
     P.npairs = z.npairs;
     P.max_items = z.max_items;
     P.dirs = d_dirs;
-    P.ctl = cv.take<int>(4);
+    P.ctl = cv.take<int>(8);
     P.perm = cv.take<int>((size_t)nsets * D);
     P.rank = cv.take<int>((size_t)nsets * D);
     P.boff = cv.take<int>((size_t)nsets * (t->NO + 1));
@@ -698,6 +720,8 @@ static EvalPlan ht_carve(const topot_tables* t, const HtSizing& z, const double*
     P.thr = nullptr;
     P.T = 0;
     *part = cv.take<double>(z.part_elems);
+    P.item_pair = cv.take<int>((size_t)z.max_items);
+    P.wide_items = cv.take<int>((size_t)z.max_items);
     return P;
 }
 
@@ -719,10 +743,10 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
         return fail(TOPOT_ERR_INVALID_ARG, std::string(name) + ": bad precision");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const HtSizing z = ht_sizing(t, kernel, precision, D, per_image_dirs, adjoint);
-    topot_status s = ensure_ws(t, z.need);
+    topot_status s = ensure_ws(t, kWsHybrid, z.need);
     if (s != TOPOT_OK) return s;
     double* part = nullptr;
-    EvalPlan P = ht_carve(t, z, d_dirs, D, per_image_dirs, t->ws, &part);
+    EvalPlan P = ht_carve(t, z, d_dirs, D, per_image_dirs, t->ws[kWsHybrid], &part);
     if (kernel == TOPOT_TABLE) {
         P.ktab = kt->d32;
         P.ktab64 = kt->d64;
@@ -735,7 +759,7 @@ static topot_status ht_common(const char* name, const topot_tables* tc, topot_ke
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
     const int per_sm = t->tuning.ht_ctas_per_sm > 0 ? t->tuning.ht_ctas_per_sm : 4;
-    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, adjoint, dl, t->sm_count * per_sm, part, st));
+    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, adjoint, dl, z.split, t->sm_count * per_sm, part, st));
     if (adjoint)
         TOPOT_CUDA(launch_ht_adj_combine(P, t->n, t->B, kernel, precision, tdh, part, d_gout, d_out, st));
     else
@@ -902,7 +926,7 @@ topot_status hybrid_transform_noalloc(const topot_tables* tc, topot_kernel kerne
     TOPOT_CUDA(launch_dir_prep(P, t->n, st));
     TOPOT_CUDA(launch_plan(P, t->dev(), st));
     const int per_sm = t->tuning.ht_ctas_per_sm > 0 ? t->tuning.ht_ctas_per_sm : 4;
-    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, false, dl, t->sm_count * per_sm, part, st));
+    TOPOT_CUDA(launch_ht(P, t->dev(), kernel, precision, false, dl, z.split, t->sm_count * per_sm, part, st));
     TOPOT_CUDA(launch_ht_combine(P, t->n, t->B, kernel, precision, tdh, part, t->slab ? t->vsum : nullptr, t->S,
                                  d_out, st));
     return TOPOT_OK;
@@ -983,9 +1007,9 @@ topot_status exact_representation(const topot_tables* tc, int kind, const double
                                                " < largest table " + std::to_string(max_n));
     const size_t slots = (size_t)nseg * (size_t)cap;
     const size_t need = 2 * slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * (size_t)nseg + 8 * 256;
-    topot_status s = ensure_ws(t, need);
+    topot_status s = ensure_ws(t, kWsExact, need);
     if (s != TOPOT_OK) return s;
-    Carver cv{reinterpret_cast<char*>(t->ws)};
+    Carver cv{reinterpret_cast<char*>(t->ws[kWsExact])};
     ExactArgs a{};
     a.t = t->dev();
     a.dirs = d_dirs;

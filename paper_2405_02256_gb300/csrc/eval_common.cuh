@@ -29,8 +29,11 @@ struct EvalPlan {
     int* rank;                 // [nsets][D]: position of each direction in its group
     int* boff;                 // [nsets][NO + 1]: group offsets
     long long* pair_items;     // [npairs + 1]: exclusive prefix of items
+    int* item_pair;            // [max_items]: the pair of every item (written by the planner)
+    int* wide_items;           // [max_items]: hybrid FP32C items for the wide-range launch
     int* pair_chunks;          // [npairs]
-    int* ctl;                  // [0] item counter, [1] chunk, [2] number of items
+    int* ctl;                  // [0] item counter, [1] chunk, [2] number of items,
+                               // [3] wide-range item counter, [4] wide-range items
     double* thr;               // [T] thresholds (ECT / Radon)
     int T;
     double t_min, t_max;
@@ -75,14 +78,11 @@ __device__ __forceinline__ int pair_segment(int mode, int NO, int o, int part, i
     return NO + o;
 }
 
-// Item -> (pair, tile, chunk) by binary search over the item prefix.
+// Item -> (pair, tile, chunk): the pair from the planner's map (one load, where a binary
+// search over tens of thousands of pairs of a ragged batch took a chain of dependent loads).
 __device__ __forceinline__ void decode_item(const EvalPlan& P, long long item, int& pair, int& tile,
                                             int& chunk) {
-    int lo = 0, hi = P.npairs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.pair_items[mid] <= item) lo = mid; else hi = mid - 1;
-    }
+    const int lo = P.item_pair[item];
     pair = lo;
     const long long local = item - P.pair_items[lo];
     const int nch = P.pair_chunks[lo];

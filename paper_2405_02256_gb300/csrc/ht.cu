@@ -392,21 +392,23 @@ __device__ __forceinline__ void kernel_pair(float2 z, float2 (&k)[2], bool mufu_
 // block adds at most 8 eps of its terms' magnitudes, the compensated sum 2 eps.  For
 // Fourier and sine the pairs on MUFU sin / cos (odd pairs), whose evaluation takes most of
 // the error budget, close their block every 4 points.
-template <int NDIM, int KERNEL, int NPR, int PATH>
-__device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we, const float2 (&w)[NPR][3],
+template <int NDIM, int KERNEL, int NPR, int PATH, int PS>
+__device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we, int g, const float2 (&w)[NPR][3],
                                                 float2 (&s2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1],
                                                 float2 (&n2)[NPR][KERNEL == TOPOT_FOURIER ? 2 : 1]) {
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
     constexpr bool SPLIT = KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE;
-    // [ws, we) is a multiple of 8 long (rounds are padded with zero-value points); each
-    // block is summed in two interleaved chains (even / odd points) to halve the
-    // dependency depth, then added with compensation.
-    for (int e = ws; e < we; e += 8) {
+    // [ws, we) is a multiple of 8 PS long (rounds are padded with zero-value points); the
+    // lanes of point group g take points ws + g, ws + g + PS, ... (with PS = 2 the two
+    // half-warps read neighbouring points: different banks, one shared-memory wavefront).
+    // Each block of 8 points is summed in two interleaved chains (even / odd points) to
+    // halve the dependency depth, then added with compensation.
+    for (int e = ws + g; e < we; e += 8 * PS) {
         float2 ba[NPR][NC], bb[NPR][NC];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const float4 qa = A[2 * (e + u)];
-            const float4 qb = A[2 * (e + u) + 1];
+            const float4 qa = A[2 * (e + u * PS)];
+            const float4 qb = A[2 * (e + u * PS) + 1];
             const float2 c0 = make_float2(qa.x, qa.y), c1 = make_float2(qa.z, qa.w);
             const float2 c2 = make_float2(qb.x, qb.y), v2 = make_float2(qb.z, qb.w);
 #pragma unroll
@@ -441,14 +443,16 @@ __device__ __forceinline__ void ht_packed_range(const float4* A, int ws, int we,
 
 // Sum of the table values of staged points [e0 + i0, e0 + i1) (one warp's slice of a
 // round), exact in 64-bit integers; every lane gets it.
-template <typename Tval>
+template <typename Tval, int PS>
 __device__ __forceinline__ long long warp_value_sum(const TablesDev& t, const HtItem& it, long long e0, int i0,
                                                     int i1, int lane) {
+    // point group g = lane / (32 / PS) sums points i0 + g, i0 + g + PS, ...
+    constexpr int GL = 32 / PS;
     const Tval* aval = reinterpret_cast<const Tval*>(t.arena_val);
     long long v = 0;
-    for (int i = i0 + lane; i < i1; i += 32) v += aval[it.base + e0 + i];
+    for (int i = i0 + lane / GL + PS * (lane % GL); i < i1; i += 32) v += aval[it.base + e0 + i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = GL / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
@@ -473,14 +477,14 @@ enum HtRole : int { kRoleAll = 0, kRolePacked = 1, kRoleWide = 2 };
 
 // Largest M = sum_k |xi_k| / 2 (a bound on |<xi, v>|) over the tile's directions; every
 // lane of the warp gets it.
-template <int NDIM, int DL>
+template <int NDIM, int TDH>
 __device__ __forceinline__ float tile_mloc(const EvalPlan& P, const HtItem& it, int tile, int lane) {
     constexpr int NO = 1 << NDIM;
     float m = 0.0f;
 #pragma unroll
-    for (int j = 0; j < DL; ++j) {
-        const int r = tile * 32 * DL + j * 32 + lane;
-        if (r < it.nd) {
+    for (int j = 0; j < (TDH + 31) / 32; ++j) {
+        const int r = tile * TDH + j * 32 + lane;
+        if (j * 32 + lane < TDH && r < it.nd) {
             const int d = P.perm[(long long)it.set * P.D + P.boff[(long long)it.set * (NO + 1) + it.o] + r];
             const double* xp = P.dirs + ((long long)it.set * P.D + d) * NDIM;
             double a = 0.0;
@@ -499,10 +503,14 @@ __device__ __forceinline__ float packed_limit() {
     return KERNEL == TOPOT_LAPLACE ? kLaplaceM32 : (KERNEL == TOPOT_BESSEL ? kBesselM32 : kTrigM32);
 }
 
-template <int NDIM, int KERNEL, int DL, typename Tval, int ROLE>
+template <int NDIM, int KERNEL, int DL, typename Tval, int ROLE, int SPL>
 __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, double* part) {
+    // SPL point groups per warp: lanes l and l + 32 / SPL hold the same DL directions and
+    // take alternate points, so a tile is 32 DL / SPL directions (SPL = 2: tiles of 32 or
+    // 64 directions with two or four directions per lane, for small direction sets)
     constexpr int NC = KERNEL == TOPOT_FOURIER ? 2 : 1;
-    constexpr int TDH = 32 * DL;
+    constexpr int GL = 32 / SPL;                // lanes per point group
+    constexpr int TDH = GL * DL;
     constexpr int NO = 1 << NDIM;
     constexpr int NPR = DL / 2;                 // direction pairs per lane (packed path)
     constexpr bool SPLIT = KERNEL == TOPOT_FOURIER || KERNEL == TOPOT_SINE;
@@ -510,32 +518,40 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
     // staging buffer: scalar path (p0, p1, p2, value) per point; packed path
     // (p0, p0, p1, p1), (p2, p2, v, v); reused for the per-item reduction
     __shared__ __align__(16) float4 A[2 * kHtSub];
-    static_assert(sizeof(double) * kHtWarps * TDH * NC <= sizeof(float4) * 2 * kHtSub, "reduction buffer");
+    static_assert(sizeof(double) * kHtWarps * SPL * TDH * NC <= sizeof(float4) * 2 * kHtSub, "reduction buffer");
     double(*red)[TDH * NC] = reinterpret_cast<double(*)[TDH * NC]>(A);
     __shared__ long long sh_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = lane / GL, gln = lane % GL;   // point group, lane within the group
     const long long nitems = P.ctl[2];
-    int* counter = ROLE == kRoleWide ? &P.ctl[3] : &P.ctl[0];
 
     while (true) {
         __syncthreads();
-        if (tid == 0) sh_item = atomicAdd(counter, 1);
+        // the wide launch takes the items the packed launch set aside (ctl[4] of them)
+        if (tid == 0) {
+            if (ROLE == kRoleWide) {
+                const int k = atomicAdd(&P.ctl[3], 1);
+                sh_item = k < P.ctl[4] ? (long long)P.wide_items[k] : nitems;
+            } else {
+                sh_item = atomicAdd(&P.ctl[0], 1);
+            }
+        }
         __syncthreads();
         const long long item = sh_item;
         if (item >= nitems) break;
         int tile;
         const HtItem it = ht_item(P, t, item, NO, TDH, tile);
         // tile-uniform choice of the evaluation path (all warps see the same tile)
-        const float mloc = tile_mloc<NDIM, DL>(P, it, tile, lane);
+        const float mloc = tile_mloc<NDIM, TDH>(P, it, tile, lane);
         const bool in_range = mloc <= packed_limit<NDIM, KERNEL>();
         // an item of the other launch: no points and no partial written (a skip that keeps
         // the loop's shape, which the packed path's register allocation prefers)
         const bool mine = !((ROLE == kRolePacked && !in_range) || (ROLE == kRoleWide && in_range));
-        if (ROLE == kRoleWide && !mine) continue;   // the wide launch skips at once
+        if (ROLE == kRolePacked && !mine && tid == 0) P.wide_items[atomicAdd(&P.ctl[4], 1)] = (int)item;
         const long long e_end = mine ? it.e_end : it.e_begin;
         HtDir hd[DL];
 #pragma unroll
-        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * 32 + lane, hd[j]);
+        for (int j = 0; j < DL; ++j) ht_dir<NDIM, KERNEL>(P, it, tile * TDH + j * GL + gln, hd[j]);
         // 0: scalar path; packed paths by the range of |<xi, v>| <= mloc:
         //   Laplace: 1 (<= 1)
         //   Fourier, sine: 3 (<= 0.5, tiny), 2 (<= 0.75, short), 1 (<= 1.75, long polynomials)
@@ -576,18 +592,18 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
 #pragma unroll
                         for (int j = 0; j < DL; ++j) {
                             double zr = -1e300;
-                            for (int e = ws; e < we; ++e) zr = fmax(zr, lap_arg64<NDIM>(A[e], hd[j].xi, inv));
+                            for (int e = ws + grp; e < we; e += SPL) zr = fmax(zr, lap_arg64<NDIM>(A[e], hd[j].xi, inv));
                             float sr = 0.0f, cr = 0.0f;
-                            for (int e = ws; e < we; ++e) {
+                            for (int e = ws + grp; e < we; e += SPL) {
                                 const float4 q = A[e];
                                 kahan_add(sr, cr, q.w * exp2f((float)(lap_arg64<NDIM>(q, hd[j].xi, inv) - zr)));
                             }
-                            off[j][0] += ((double)sr - (double)cr) * exp2(zr);
+                            if (zr > -1e300) off[j][0] += ((double)sr - (double)cr) * exp2(zr);
                         }
                     }
                     continue;
                 }
-                for (int e = ws; e < we; ++e) {
+                for (int e = ws + grp; e < we; e += SPL) {
                     const float4 q = A[e];
 #pragma unroll
                     for (int j = 0; j < DL; ++j) {
@@ -635,16 +651,18 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             for (long long e0 = it.e_begin; e0 < e_end; e0 += kHtSub) {
                 const int cnt = (int)min((long long)kHtSub, e_end - e0);
                 __syncthreads();
-                // pad the round to 8 points per warp per block with zero-value points
-                const int cnt_pad = (cnt + kHtWarps * 8 - 1) / (kHtWarps * 8) * (kHtWarps * 8);
+                // pad the round to 8 points per warp and point group with zero-value points
+                const int cnt_pad = (cnt + kHtWarps * 8 * SPL - 1) / (kHtWarps * 8 * SPL) * (kHtWarps * 8 * SPL);
                 ht_stage<NDIM, KERNEL, false, Tval, true>(t, it, e0, cnt, A, nullptr, cnt_pad);
                 __syncthreads();
                 const int per = cnt_pad / kHtWarps;
                 const int ws = warp * per, we = ws + per;
-                if (SPLIT && NPR > 1) vsum += warp_value_sum<Tval>(t, it, e0, ws, min(we, cnt), lane);
-                if (KERNEL != TOPOT_LAPLACE && path == 3) ht_packed_range<NDIM, KERNEL, NPR, 3>(A, ws, we, w, s2, n2);
-                else if (KERNEL != TOPOT_LAPLACE && path == 2) ht_packed_range<NDIM, KERNEL, NPR, 2>(A, ws, we, w, s2, n2);
-                else ht_packed_range<NDIM, KERNEL, NPR, 1>(A, ws, we, w, s2, n2);
+                if (SPLIT && NPR > 1) vsum += warp_value_sum<Tval, SPL>(t, it, e0, ws, min(we, cnt), lane);
+                if (KERNEL != TOPOT_LAPLACE && path == 3)
+                    ht_packed_range<NDIM, KERNEL, NPR, 3, SPL>(A, ws, we, grp, w, s2, n2);
+                else if (KERNEL != TOPOT_LAPLACE && path == 2)
+                    ht_packed_range<NDIM, KERNEL, NPR, 2, SPL>(A, ws, we, grp, w, s2, n2);
+                else ht_packed_range<NDIM, KERNEL, NPR, 1, SPL>(A, ws, we, grp, w, s2, n2);
             }
 #pragma unroll
             for (int pq = 0; pq < NPR; ++pq)
@@ -666,13 +684,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             {
                 double r = (double)acc[j][c] + (double)cmp[j][c];
                 if constexpr (ROLE != kRolePacked || SPLIT) r += off[j][c];
-                red[warp][(j * 32 + lane) * NC + c] = r;
+                red[warp * SPL + grp][(j * GL + gln) * NC + c] = r;
             }
         __syncthreads();
         for (int i = tid; mine && i < TDH * NC; i += kHtBlock) {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < kHtWarps; ++w) s += red[w][i];
+            for (int w = 0; w < kHtWarps * SPL; ++w) s += red[w][i];
             part[item * (TDH * NC) + i] = s;
         }
     }
@@ -1001,22 +1019,29 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
     __shared__ long long sh_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long nitems = P.ctl[2];
-    int* counter = ROLE == kRoleWide ? &P.ctl[3] : &P.ctl[0];
 
     while (true) {
         __syncthreads();
-        if (tid == 0) sh_item = atomicAdd(counter, 1);
+        // the wide launch takes the items the packed launch set aside (ctl[4] of them)
+        if (tid == 0) {
+            if (ROLE == kRoleWide) {
+                const int k = atomicAdd(&P.ctl[3], 1);
+                sh_item = k < P.ctl[4] ? (long long)P.wide_items[k] : nitems;
+            } else {
+                sh_item = atomicAdd(&P.ctl[0], 1);
+            }
+        }
         __syncthreads();
         const long long item = sh_item;
         if (item >= nitems) break;
         int tile;
         const HtItem it = ht_item(P, t, item, NO, TDH, tile);
-        const float mloc = tile_mloc<NDIM, DL>(P, it, tile, lane);
+        const float mloc = tile_mloc<NDIM, TDH>(P, it, tile, lane);
         const bool in_range = mloc <= packed_limit<NDIM, KERNEL>();
         // an item of the other launch: no points and no partial written (a skip that keeps
         // the loop's shape, which the packed path's register allocation prefers)
         const bool mine = !((ROLE == kRolePacked && !in_range) || (ROLE == kRoleWide && in_range));
-        if (ROLE == kRoleWide && !mine) continue;   // the wide launch skips at once
+        if (ROLE == kRolePacked && !mine && tid == 0) P.wide_items[atomicAdd(&P.ctl[4], 1)] = (int)item;
         const long long e_end = mine ? it.e_end : it.e_begin;
         HtDir hd[DL];
 #pragma unroll
@@ -1351,9 +1376,16 @@ __global__ void k_ht_adj_combine(EvalPlan P, int n, int B, int kernel, int preci
 
 // ---- launchers ---------------------------------------------------------------------------------
 
+template <int NDIM, int KERNEL, int DL, typename Tval, int SPL>
+static void launch_fwd_pair(const EvalPlan& P, const TablesDev& t, int grid, int wide_grid, double* part,
+                            cudaStream_t st) {
+    k_ht_f32<NDIM, KERNEL, DL, Tval, kRolePacked, SPL><<<grid, kHtBlock, 0, st>>>(P, t, part);
+    k_ht_f32<NDIM, KERNEL, DL, Tval, kRoleWide, SPL><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+}
+
 template <int NDIM, int KERNEL, typename Tval>
 static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precision, bool adjoint, int dl,
-                               int grid, double* part, cudaStream_t st) {
+                               int split, int grid, double* part, cudaStream_t st) {
     if (precision == TOPOT_FP64) {
         if (adjoint) k_ht_adj_f64<NDIM, KERNEL, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
         else k_ht_f64<NDIM, KERNEL, Tval><<<grid, kHtBlock, 0, st>>>(P, t, part);
@@ -1379,20 +1411,20 @@ static cudaError_t launch_ht_k(const EvalPlan& P, const TablesDev& t, int precis
             default: return cudaErrorInvalidValue;
         }
     } else {
+        if (split != 1 && (split != 2 || (dl != 2 && dl != 4))) return cudaErrorInvalidValue;
         switch (dl) {
-            case 1: k_ht_f32<NDIM, KERNEL, 1, Tval, kRoleAll><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
+            case 1: k_ht_f32<NDIM, KERNEL, 1, Tval, kRoleAll, 1><<<grid, kHtBlock, 0, st>>>(P, t, part); break;
             case 2:
-                k_ht_f32<NDIM, KERNEL, 2, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
-                k_ht_f32<NDIM, KERNEL, 2, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                if (split == 2) launch_fwd_pair<NDIM, KERNEL, 2, Tval, 2>(P, t, grid, wide_grid, part, st);
+                else launch_fwd_pair<NDIM, KERNEL, 2, Tval, 1>(P, t, grid, wide_grid, part, st);
                 break;
             case 4:
-                k_ht_f32<NDIM, KERNEL, 4, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
-                k_ht_f32<NDIM, KERNEL, 4, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                if (split == 2) launch_fwd_pair<NDIM, KERNEL, 4, Tval, 2>(P, t, grid, wide_grid, part, st);
+                else launch_fwd_pair<NDIM, KERNEL, 4, Tval, 1>(P, t, grid, wide_grid, part, st);
                 break;
             case 8:
                 if (KERNEL != TOPOT_LAPLACE) return cudaErrorInvalidValue;
-                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval, kRolePacked><<<grid, kHtBlock, 0, st>>>(P, t, part);
-                k_ht_f32<NDIM, TOPOT_LAPLACE, 8, Tval, kRoleWide><<<wide_grid, kHtBlock, 0, st>>>(P, t, part);
+                launch_fwd_pair<NDIM, TOPOT_LAPLACE, 8, Tval, 1>(P, t, grid, wide_grid, part, st);
                 break;
             default: return cudaErrorInvalidValue;
         }
@@ -1434,12 +1466,16 @@ static cudaError_t launch_ht_table(const EvalPlan& P, const TablesDev& t, int pr
 
 template <int NDIM, typename Tval>
 static cudaError_t launch_ht_n(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint,
-                               int dl, int grid, double* part, cudaStream_t st) {
+                               int dl, int split, int grid, double* part, cudaStream_t st) {
     switch (kernel) {
-        case TOPOT_LAPLACE: return launch_ht_k<NDIM, TOPOT_LAPLACE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
-        case TOPOT_FOURIER: return launch_ht_k<NDIM, TOPOT_FOURIER, Tval>(P, t, precision, adjoint, dl, grid, part, st);
-        case TOPOT_BESSEL: return launch_ht_k<NDIM, TOPOT_BESSEL, Tval>(P, t, precision, adjoint, dl, grid, part, st);
-        case TOPOT_SINE: return launch_ht_k<NDIM, TOPOT_SINE, Tval>(P, t, precision, adjoint, dl, grid, part, st);
+        case TOPOT_LAPLACE:
+            return launch_ht_k<NDIM, TOPOT_LAPLACE, Tval>(P, t, precision, adjoint, dl, split, grid, part, st);
+        case TOPOT_FOURIER:
+            return launch_ht_k<NDIM, TOPOT_FOURIER, Tval>(P, t, precision, adjoint, dl, split, grid, part, st);
+        case TOPOT_BESSEL:
+            return launch_ht_k<NDIM, TOPOT_BESSEL, Tval>(P, t, precision, adjoint, dl, split, grid, part, st);
+        case TOPOT_SINE:
+            return launch_ht_k<NDIM, TOPOT_SINE, Tval>(P, t, precision, adjoint, dl, split, grid, part, st);
         case TOPOT_TABLE: return launch_ht_table<NDIM, Tval>(P, t, precision, adjoint, dl, grid, part, st);
         default: return cudaErrorInvalidValue;
     }
@@ -1449,14 +1485,15 @@ cudaError_t launch_ht_gen(const EvalPlan& P, const TablesDev& t, int kernel, int
                           double* part, cudaStream_t st);
 
 cudaError_t launch_ht(const EvalPlan& P, const TablesDev& t, int kernel, int precision, bool adjoint, int dl,
-                      int grid, double* part, cudaStream_t st) {
+                      int split, int grid, double* part, cudaStream_t st) {
     if (t.n == 4) return launch_ht_gen(P, t, kernel, precision, adjoint, grid, part, st);   // dl = 1
     if (t.n == 2) {
-        if (t.val_bytes == 2) return launch_ht_n<2, int16_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
-        return launch_ht_n<2, int32_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+        if (t.val_bytes == 2)
+            return launch_ht_n<2, int16_t>(P, t, kernel, precision, adjoint, dl, split, grid, part, st);
+        return launch_ht_n<2, int32_t>(P, t, kernel, precision, adjoint, dl, split, grid, part, st);
     }
-    if (t.val_bytes == 2) return launch_ht_n<3, int16_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
-    return launch_ht_n<3, int32_t>(P, t, kernel, precision, adjoint, dl, grid, part, st);
+    if (t.val_bytes == 2) return launch_ht_n<3, int16_t>(P, t, kernel, precision, adjoint, dl, split, grid, part, st);
+    return launch_ht_n<3, int32_t>(P, t, kernel, precision, adjoint, dl, split, grid, part, st);
 }
 
 cudaError_t launch_ht_combine(const EvalPlan& P, int n, int B, int kernel, int precision, int tdh,

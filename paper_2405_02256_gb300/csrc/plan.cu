@@ -202,9 +202,10 @@ __global__ void __launch_bounds__(1024) k_plan(EvalPlan P, TablesDev t) {
         }
         chunk_sh = chunk;
         carry = 0;
-        P.ctl[0] = 0;   // item counter (second counter ctl[3]: wide hybrid-transform tiles)
+        P.ctl[0] = 0;   // item counter
         P.ctl[1] = chunk;
-        P.ctl[3] = 0;
+        P.ctl[3] = 0;   // hybrid transforms: wide-range items taken, and set aside
+        P.ctl[4] = 0;
     }
     __syncthreads();
     const int chunk = chunk_sh;
@@ -241,15 +242,19 @@ __global__ void __launch_bounds__(1024) k_plan(EvalPlan P, TablesDev t) {
         }
         __syncthreads();
         const long long excl = carry + (warp ? (long long)red[warp - 1] : 0) + v - items;
-        if (p < P.npairs) P.pair_items[p] = excl;
+        if (p < P.npairs) {
+            P.pair_items[p] = excl;
+            // item -> pair map (items past the buffers' bound are never run)
+            for (long long i = excl; i < excl + items && i < P.max_items; ++i) P.item_pair[i] = p;
+        }
         __syncthreads();
         if (tid == 0) carry += (long long)red[31];
         __syncthreads();
     }
     if (tid == 0) {
         P.pair_items[P.npairs] = carry;
-        // never run more items than the partial buffers hold (cannot happen with the
-        // host's bound; recorded as an error if it ever does)
+        // never run more items than the buffers hold (cannot happen with the host's
+        // bound; recorded as an error if it ever does)
         if (carry > P.max_items) dev_set_error(t.err, kDevErrOverflow);
         P.ctl[2] = (int)(carry > P.max_items ? P.max_items : carry);
     }

@@ -82,10 +82,11 @@ def test_forward_bands(tb, kernel, n, band):
     dirs = band_dirs(n, 72, 310 + n, lo, hi)
     d = torch.from_numpy(dirs).cuda()
     want, norm = O.hybrid_transform(ref, kernel, dirs)
-    for dl in ([1, 2, 4, 8] if kernel == "laplace" else [1, 2, 4]):
-        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+    tiles = [(1, 1), (2, 1), (4, 1), (2, 2), (4, 2)] + ([(8, 1)] if kernel == "laplace" else [])
+    for dl, split in tiles:   # directions per lane, point groups per warp
+        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024, ht_warp_split=split)
         got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
-        assert _fwd_err(got, want, norm, kernel) <= 1e-6, (dl, _fwd_err(got, want, norm, kernel))
+        assert _fwd_err(got, want, norm, kernel) <= 1e-6, (dl, split, _fwd_err(got, want, norm, kernel))
     got = tb.hybrid_transform(tabs, kernel, d, "fp64").cpu().numpy()[0]
     assert _fwd_err(got, want, norm, kernel) <= 1e-12
 
@@ -122,8 +123,8 @@ def test_mixed_bands_one_call(tb, kernel):
     dirs = np.concatenate([band_dirs(2, 40, 330 + i, lo, hi) for i, (lo, hi) in enumerate(BANDS.values())])
     d = torch.from_numpy(dirs).cuda()
     want, norm = O.hybrid_transform(ref, kernel, dirs)
-    for dl in (2, 4):
-        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024)
+    for dl, split in ((2, 1), (4, 1), (2, 2), (4, 2)):
+        tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=1024, ht_warp_split=split)
         got = tb.hybrid_transform(tabs, kernel, d).cpu().numpy()[0]
         assert _fwd_err(got, want, norm, kernel) <= 1e-6
 

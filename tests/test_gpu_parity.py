@@ -189,12 +189,12 @@ def test_hybrid_transform(tb, kernel, precision, name):
     assert _ht_err(got, want, norm, kernel) <= HT_TOL[precision]
 
 
-@pytest.mark.parametrize("dl", [1, 2, 4, 8])
-def test_hybrid_transform_tiles(tb, dl):
+@pytest.mark.parametrize("dl,split", [(1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2)])
+def test_hybrid_transform_tiles(tb, dl, split):
     img = synth.grf((200, 180), 6.0, seed=50)
     ref = O.critical_tables(img)
     tabs = tb.build_critical_tables(tb.pack_images([img]))
-    tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=2048)
+    tabs.set_tuning(ht_dirs_per_lane=dl, ht_chunk=2048, ht_warp_split=split)
     dirs = synth.random_2d_dirs(1100, 51, 0.01, 1.0)
     d = torch.from_numpy(dirs).cuda()
     for kernel in ("laplace", "fourier", "bessel", "sine") if dl < 8 else ("laplace",):
