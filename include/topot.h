@@ -85,8 +85,8 @@ typedef enum { TOPOT_VERTEX = 0, TOPOT_TOP = 1 } topot_construction;
 typedef enum { TOPOT_LAPLACE = 0, TOPOT_FOURIER = 1, TOPOT_BESSEL = 2, TOPOT_SINE = 3, TOPOT_TABLE = 4 } topot_kernel;
 
 /* FP32C: FP32 terms, Kahan-compensated per thread, FP64 cross-block combine
- *        (Laplace evaluated as e^{M} e^{s - M}, M = sum_k |xi_k| / 2, so no term
- *        overflows).  FP64: plain FP64 terms and sums. */
+ *        (Laplace terms beyond |s| <= 1 are scaled per round of points, so no FP32
+ *        term overflows or underflows).  FP64: plain FP64 terms and sums. */
 typedef enum { TOPOT_FP32C = 0, TOPOT_FP64 = 1 } topot_precision;
 
 typedef struct topot_tables topot_tables;   /* opaque; owns the device tables */
@@ -267,7 +267,8 @@ TOPOT_API topot_status radon_exact_eval(int nrep, int64_t cap, const double* d_T
  * [B][D][2] (FOURIER: re, im).  Deterministic for a given tuning and direction set.
  * Accuracy, with M = sum_k |xi_k| / 2 >= |<xi, v>|:
  *   FP32C: |HT - exact| <= 1e-6 sum_v |Delta kbar(<xi, v>)| (complex modulus for FOURIER)
- *     for every finite xi with M <= 1e6; LAPLACE needs M <= 300 and returns NaN beyond.
+ *     for every finite xi with M <= 1e6; LAPLACE overflows (inf or NaN) once some
+ *     <xi, v> exceeds ~709, as in FP64.
  *     The terms are kbar(s) - kbar(0) (the constant cancels: sum_v Delta_eps(v) = 0),
  *     so transforms much smaller than that bound (small |xi|) keep their relative
  *     accuracy; tiles with M above 1 (LAPLACE), 1.75 (FOURIER, SINE) or 2 (BESSEL)

@@ -685,7 +685,7 @@ static HtSizing ht_sizing(const topot_tables* t, topot_kernel kernel, topot_prec
     z.tdh = 32 * z.dl / z.split;
     const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
     z.ncomp = adjoint ? nk * t->n : nk;
-    z.npairs = t->B * NO;
+    z.npairs = t->B * NO / 2;   // (image, representative orthant): an orthant shares tiles with its partner
     z.target = t->sm_count * 16;
     z.max_items = plan_max_items(t, D, z.tdh, t->tuning.ht_chunk, 1, z.target);
     z.part_elems = (size_t)z.max_items * z.tdh * z.ncomp;

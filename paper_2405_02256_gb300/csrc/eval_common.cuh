@@ -53,16 +53,31 @@ __device__ __forceinline__ int orthant_of(const double* xi, int n) {
     return o;
 }
 
-// Pair -> (image, orthant, part).
+// Pair -> (image, orthant, part).  Hybrid transforms pair an image with a representative
+// orthant r < 2^(n-1): the directions of r and of its partner r ^ (2^n - 1) evaluate the
+// same Delta table (Delta_{-eps} = -Delta_eps, the sign applied per direction at the
+// combine), so they share tiles.
 __device__ __forceinline__ void decode_pair(int mode, int NO, int p, int& b, int& o, int& part) {
+    part = 0;
+    if (mode == kModeHT) {
+        b = p / (NO / 2);
+        o = p - b * (NO / 2);
+        return;
+    }
     if (mode == kModeRadon) {
         part = p & 1;
         p >>= 1;
-    } else {
-        part = 0;
     }
     b = p / NO;
     o = p - b * NO;
+}
+
+// Direction group of a direction: its orthant, or for hybrid transforms the
+// representative of its orthant's pair.
+__device__ __forceinline__ int dir_group(const double* xi, int n, int mode) {
+    const int o = orthant_of(xi, n);
+    const int NO = 1 << n;
+    return (mode == kModeHT && (o & (NO >> 1))) ? (o ^ (NO - 1)) : o;
 }
 
 // Segment (table) used by a pair, and the sign applied to its values.

@@ -406,8 +406,8 @@ __global__ void __launch_bounds__(kGenBlock) k_hist_gen(EvalPlan P, TablesDev t,
     }
 }
 
-// (s - M) log2 e in FP64 from the canonical dot product.
-__device__ __forceinline__ double gen_lap_exp(double s, double M) { return (s - M) * 1.4426950408889634; }
+// s log2 e in FP64 from the canonical dot product.
+__device__ __forceinline__ double gen_lap_exp(double s) { return s * 1.4426950408889634; }
 
 // Forward (ADJ = false) or adjoint of the hybrid transform, one direction per lane.
 template <int NDIM, int KERNEL, bool ADJ, typename Tval>
@@ -437,13 +437,9 @@ __global__ void __launch_bounds__(kGenBlock) k_ht_gen(EvalPlan P, TablesDev t, i
         const int r = tile * 32 + lane;
         const bool valid = r < bo[o + 1] - bo[o];
         const int d = valid ? P.perm[(long long)set * P.D + bo[o] + r] : 0;
-        double xi[NDIM], M = 0.0;
+        double xi[NDIM];
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-            xi[k] = P.dirs[((long long)set * P.D + d) * NDIM + k];
-            M += fabs(xi[k]);
-        }
-        M *= 0.5;
+        for (int k = 0; k < NDIM; ++k) xi[k] = P.dirs[((long long)set * P.D + d) * NDIM + k];
         const long long N = t.seg_count[(long long)b * t.S + seg];
         const long long base = I.seg_base + (long long)seg * I.N;
         const long long e_begin = (long long)ch * P.ctl[1], e_end = min(N, e_begin + P.ctl[1]);
@@ -480,13 +476,13 @@ __global__ void __launch_bounds__(kGenBlock) k_ht_gen(EvalPlan P, TablesDev t, i
                 // FP64 exponents, the round scaled by its largest term
                 if (ws < we) {
                     double zr = -1e300;
-                    for (int e = ws; e < we; ++e) zr = fmax(zr, gen_lap_exp(gen_dot<NDIM>(xi, X[e]), M));
+                    for (int e = ws; e < we; ++e) zr = fmax(zr, gen_lap_exp(gen_dot<NDIM>(xi, X[e])));
                     float sr[NC], cr[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) sr[c] = cr[c] = 0.0f;
                     for (int e = ws; e < we; ++e) {
                         const float tk =
-                            (float)V[e] * exp2f((float)(gen_lap_exp(gen_dot<NDIM>(xi, X[e]), M) - zr));
+                            (float)V[e] * exp2f((float)(gen_lap_exp(gen_dot<NDIM>(xi, X[e])) - zr));
 #pragma unroll
                         for (int c = 0; c < NC; ++c) kahan_add_gen(sr[c], cr[c], ADJ ? tk * (float)X[e][c] : tk);
                     }

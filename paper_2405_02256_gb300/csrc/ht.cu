@@ -19,11 +19,10 @@
 // drops out of the closed form because sum_v Delta_eps(v) = 0 over a whole table, and
 // without it a term stays small where kbar(s) is close to kbar(0) (cos s - 1 = -w q(w),
 // J0 - 1 = -y q(y) on the polynomial paths), so small transforms keep their accuracy.
-// Laplace uses e^s = e^M e^{s - M} with M = sum_k |xi_k| / 2 = max_v s_v:
-// s - M = sum_k (|xi_k| / (m_k - 1)) q_k with integer q_k <= 0, so every FP32 exponent
-// is <= 0 (no overflow) and is a sum of non-positive terms (no cancellation); for
-// M <= 40 no term underflows either, beyond that the scalar path rescales each round of
-// staged points by its own largest term.
+// Laplace: the packed path takes tiles with M = sum_k |xi_k| / 2 <= 1 (|s| <= M), so the
+// terms e^s = 2^{s log2 e} lie in [1/e, e] and are summed as they are; wider tiles form
+// s log2 e in FP64 and scale every round of staged points by its own largest term, the
+// round's sum entering the FP64 partial times that term (no FP32 overflow or underflow).
 // Arguments: the packed paths form <xi, v> in FP32 (absolute error <= 3 * 2^-24 M,
 // M <= 2); the scalar path does the same up to |s| <= 1.75 (Fourier, sine) or 2
 // (Bessel) and beyond forms s in FP64 and reduces it modulo 2 pi in FP64 before the
@@ -52,10 +51,9 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float term) {
 
 // Range limits of the FP32 argument paths, by kernel (largest M = sum_k |xi_k| / 2 of a
 // tile, which bounds |<xi, v>|): beyond them the scalar path forms the argument in FP64.
-constexpr float kLaplaceM32 = 1.0f;     // Laplace: relative error of e^{s-M} <= 6 M 2^-24
+constexpr float kLaplaceM32 = 1.0f;     // Laplace: relative error of e^s <= 3 M log2(e) ln(2) 2^-24
 constexpr float kTrigM32 = 1.75f;       // Fourier, sine: polynomial and MUFU range
 constexpr float kBesselM32 = 2.0f;      // Bessel: polynomial range
-constexpr double kLaplaceMaxM = 300.0;  // FP32C Laplace: larger M gives NaN
 
 // ---- polynomial kernels -----------------------------------------------------------------------
 // Degree-d Chebyshev interpolants on [0, X] written in the power basis (constants derived
@@ -230,7 +228,7 @@ __device__ __forceinline__ float j1_scalar(float z, const float4& q, const doubl
 
 // Per-lane direction coefficients.
 struct HtDir {
-    float w[3];      // LAPLACE: |xi_k| / (m_k - 1) * log2 e; others: xi_k / (2 (m_k - 1))
+    float w[3];      // xi_k / (2 (m_k - 1)) (LAPLACE: times log2 e, so that z = sum_k w_k c_k = s log2 e)
     double xi[3];
     bool valid;
     int d;
@@ -263,8 +261,8 @@ __device__ __forceinline__ HtItem ht_item(const EvalPlan& P, const TablesDev& t,
     return it;
 }
 
-// Stage critical points [e0, e0 + cnt) as lattice data: A = (p0, p1, p2, value) with
-// p = q (LAPLACE: q_k = i_k - (m_k - 1) if eps_k = +1 else -i_k) or c_k = 2 i_k - (m_k - 1);
+// Stage critical points [e0, e0 + cnt) as lattice data: A = (p0, p1, p2, value) with the
+// lattice integers p_k = c_k = 2 i_k - (m_k - 1) (the same for an orthant and its partner);
 // X = (x0, x1, x2) embedding coordinates (adjoint only).
 template <int NDIM, int KERNEL, bool WITH_X, typename Tval, bool PACKED = false>
 __device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, long long e0, int cnt,
@@ -294,10 +292,7 @@ __device__ __forceinline__ void ht_stage(const TablesDev& t, const HtItem& it, l
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             c[k] = (float)(2 * ii[k] - (I.m[k] - 1));
-            if (KERNEL == TOPOT_LAPLACE)
-                p[k] = ((it.o >> k) & 1) ? (float)(-ii[k]) : (float)(ii[k] - (I.m[k] - 1));
-            else
-                p[k] = c[k];
+            p[k] = c[k];
         }
         if (NDIM == 2) p[2] = 0.0f;
         if (PACKED) {
@@ -321,14 +316,12 @@ __device__ __forceinline__ void ht_dir(const EvalPlan& P, const HtItem& it, int 
     hd.valid = r < it.nd;
     hd.d = hd.valid ? P.perm[(long long)it.set * P.D + P.boff[(long long)it.set * (NO + 1) + it.o] + r] : 0;
     const double* xp = P.dirs + ((long long)it.set * P.D + hd.d) * NDIM;
-    // 2 log2(e) for Laplace (|xi_k| / (m_k - 1) log2 e), 1 otherwise (xi_k / (2 (m_k - 1)))
-    const double f = KERNEL == TOPOT_LAPLACE ? 2.8853900817779268 : 1.0;
+    // Laplace works in log2 units (ex2): w_k = xi_k log2 e / (2 (m_k - 1))
+    const double f = KERNEL == TOPOT_LAPLACE ? 1.4426950408889634 : 1.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         hd.xi[k] = k < NDIM ? xp[k] : 0.0;
-        if (k >= NDIM) hd.w[k] = 0.0f;
-        else if (KERNEL == TOPOT_LAPLACE) hd.w[k] = (float)(fabs(hd.xi[k]) * (f * it.I->inv2m[k]));
-        else hd.w[k] = (float)(hd.xi[k] * it.I->inv2m[k]);
+        hd.w[k] = k < NDIM ? (float)(hd.xi[k] * (f * it.I->inv2m[k])) : 0.0f;
     }
 }
 
@@ -456,14 +449,14 @@ __device__ __forceinline__ long long warp_value_sum(const TablesDev& t, const Ht
     return v;
 }
 
-// Laplace exponent in FP64 for the scalar path: (s - M) log2 e = sum_k q_k |xi_k| / (m_k - 1)
-// log2 e from the staged integers q_k <= 0.
+// Laplace exponent in FP64 for the scalar path: s log2 e from the staged lattice integers
+// c_k (s = sum_k c_k xi_k / (2 (m_k - 1))).
 template <int NDIM>
-__device__ __forceinline__ double lap_arg64(const float4& q, const double (&xi)[3], const double (&invm)[3]) {
+__device__ __forceinline__ double lap_arg64(const float4& q, const double (&xi)[3], const double (&inv2m)[3]) {
     constexpr double kLog2e = 1.4426950408889634;
-    double s = (double)q.x * (fabs(xi[0]) * invm[0]);
-    s = fma((double)q.y, fabs(xi[1]) * invm[1], s);
-    if (NDIM == 3) s = fma((double)q.z, fabs(xi[2]) * invm[2], s);
+    double s = (double)q.x * (xi[0] * inv2m[0]);
+    s = fma((double)q.y, xi[1] * inv2m[1], s);
+    if (NDIM == 3) s = fma((double)q.z, xi[2] * inv2m[2], s);
     return s * kLog2e;
 }
 
@@ -573,13 +566,13 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             }
 
         if constexpr (ROLE != kRolePacked) {
-            // Laplace with large M: FP64 exponents, each round of staged points scaled by
-            // its own largest term (no underflow, error independent of M)
+            // Laplace beyond the packed range: FP64 exponents, each round of staged points
+            // scaled by its own largest term (no overflow or underflow, error independent of M)
             const bool rescale = KERNEL == TOPOT_LAPLACE && mloc > kLaplaceM32;
-            double inv[3];   // Laplace: 1 / (m_k - 1); others: 1 / (2 (m_k - 1))
+            double inv[3];   // 1 / (2 (m_k - 1))
 #pragma unroll
             for (int k = 0; k < 3; ++k)
-                inv[k] = k < NDIM ? (KERNEL == TOPOT_LAPLACE ? 2.0 : 1.0) * it.I->inv2m[k] : 0.0;
+                inv[k] = k < NDIM ? it.I->inv2m[k] : 0.0;
             for (long long e0 = it.e_begin; e0 < e_end; e0 += kHtSub) {
                 const int cnt = (int)min((long long)kHtSub, e_end - e0);
                 __syncthreads();
@@ -635,7 +628,7 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_f32(EvalPlan P, TablesDev t, do
             (void)in_range;
             // packed coefficients: pair p covers directions 2p and 2p + 1 of this lane;
             // Bessel uses z / 2 so that y = (z / 2)^2 is one multiply
-            float2 w[NPR][3];
+            float2 w[NPR][3];   // (w_0, w_1, w_2) of the pair's two directions
             const float wsc = KERNEL == TOPOT_BESSEL ? 0.5f : 1.0f;
 #pragma unroll
             for (int pq = 0; pq < NPR; ++pq)
@@ -1071,15 +1064,10 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
                     for (int r = 0; r < NPR; ++r)
                         w[r][k] = make_float2(wsc * hd[2 * r].w[k], wsc * hd[2 * r + 1].w[k]);
                     const float mk1 = (float)(it.I->m[k] - 1);
-                    if (KERNEL == TOPOT_LAPLACE) {   // x = sigma (q / (m - 1) + 1/2), sigma = eps_k
-                        const float sg = ((it.o >> k) & 1) ? -1.0f : 1.0f;
-                        xa[k] = make_float2(sg / mk1, sg / mk1);
-                        xb[k] = make_float2(0.5f * sg, 0.5f * sg);
-                    } else {                          // x = c / (2 (m - 1))
-                        xa[k] = make_float2(0.5f / mk1, 0.5f / mk1);
-                        xb[k] = make_float2(0.0f, 0.0f);
-                    }
+                    xa[k] = make_float2(0.5f / mk1, 0.5f / mk1);   // x = c / (2 (m - 1))
+                    xb[k] = make_float2(0.0f, 0.0f);
                 }
+
                 float2 s2[NPR][NC], n2[NPR][NC];
 #pragma unroll
                 for (int r = 0; r < NPR; ++r)
@@ -1108,10 +1096,10 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f32(EvalPlan P, TablesDev t
             }
         }
         const bool rescale = KERNEL == TOPOT_LAPLACE && mloc > kLaplaceM32;
-        double inv[3];   // Laplace: 1 / (m_k - 1); others: 1 / (2 (m_k - 1))
+        double inv[3];   // 1 / (2 (m_k - 1))
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            inv[k] = k < NDIM ? (KERNEL == TOPOT_LAPLACE ? 2.0 : 1.0) * it.I->inv2m[k] : 0.0;
+            inv[k] = k < NDIM ? it.I->inv2m[k] : 0.0;
         for (long long e0 = it.e_begin; ROLE != kRolePacked && e0 < e_end; e0 += SUB) {
             const int cnt = (int)min((long long)SUB, e_end - e0);
             __syncthreads();
@@ -1287,12 +1275,15 @@ __global__ void __launch_bounds__(kHtBlock) k_ht_adj_f64(EvalPlan P, TablesDev t
 
 // ---- combine (K6) ------------------------------------------------------------------------------
 
-// Sum of the chunk partials of direction d of image b, in chunk order.
+// Sum of the chunk partials of direction d of image b, in chunk order.  The hybrid
+// transforms group a direction with those of its orthant's partner (same Delta table):
+// pair (b, representative orthant).
 __device__ __forceinline__ void gather_partials(const EvalPlan& P, int NO, int tdh, int ncomp, int b, int d,
                                                 int o, const double* part, double* outc) {
     const int set = P.nsets == 1 ? 0 : b;
     const int r = P.rank[(long long)set * P.D + d];
-    const int pair = b * NO + o;
+    const int rep = (o & (NO >> 1)) ? (o ^ (NO - 1)) : o;
+    const int pair = b * (NO / 2) + rep;
     const int tile = r / tdh, dd = r - tile * tdh;
     const long long nitems = P.pair_items[pair + 1] - P.pair_items[pair];
     for (int c = 0; c < ncomp; ++c) outc[c] = 0.0;
@@ -1329,12 +1320,6 @@ __global__ void k_ht_combine(EvalPlan P, int n, int B, int kernel, int precision
     const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
     // sine: the partials hold sum v (cos s - 1), kbar = -cos
     double scale = kernel == TOPOT_SINE ? -sign : sign;
-    if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
-        double M = 0.0;
-        for (int k = 0; k < n; ++k) M += fabs(xi[k]);
-        M *= 0.5;
-        scale = M <= kLaplaceMaxM ? scale * exp(M) : __longlong_as_double(0x7ff8000000000000ll);
-    }
     for (int c = 0; c < nc; ++c) out[gid * nc + c] = v[c] * scale;
 }
 
@@ -1351,13 +1336,7 @@ __global__ void k_ht_adj_combine(EvalPlan P, int n, int B, int kernel, int preci
     const int nk = kernel == TOPOT_FOURIER ? 2 : 1;
     const int nc = nk * n;
     const double sign = (o & (NO >> 1)) ? -1.0 : 1.0;
-    double scale = sign;
-    if (kernel == TOPOT_LAPLACE && precision == TOPOT_FP32C) {
-        double M = 0.0;
-        for (int k = 0; k < n; ++k) M += fabs(xi[k]);
-        M *= 0.5;
-        scale = M <= kLaplaceMaxM ? scale * exp(M) : __longlong_as_double(0x7ff8000000000000ll);
-    }
+    const double scale = sign;
     double g[kMaxDim] = {0.0, 0.0, 0.0, 0.0};
     const int b0 = P.nsets == 1 ? 0 : set, b1 = P.nsets == 1 ? B : set + 1;
     for (int b = b0; b < b1; ++b) {

@@ -5,7 +5,8 @@
 
 namespace topot {
 
-// One block per direction set: stable counting sort of the directions by orthant.
+// One block per direction set: stable counting sort of the directions by group (orthant;
+// for hybrid transforms the representative of the orthant's pair).
 template <int NO>
 __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
     constexpr int NW = 1024 / 32;
@@ -17,7 +18,7 @@ __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
     const double* dirs = P.dirs + (long long)set * P.D * n;
     if (tid < NO) cnt[tid] = 0;
     __syncthreads();
-    for (int d = tid; d < P.D; d += 1024) atomicAdd(&cnt[orthant_of(dirs + (long long)d * n, n)], 1);
+    for (int d = tid; d < P.D; d += 1024) atomicAdd(&cnt[dir_group(dirs + (long long)d * n, n, P.mode)], 1);
     __syncthreads();
     if (tid == 0) {
         int run = 0;
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
     int* perm = P.perm + (long long)set * P.D;
     for (int d0 = 0; d0 < P.D; d0 += 1024) {
         const int d = d0 + tid;
-        const int o = d < P.D ? orthant_of(dirs + (long long)d * n, n) : -1;
+        const int o = d < P.D ? dir_group(dirs + (long long)d * n, n, P.mode) : -1;
         int myrank = 0;
 #pragma unroll
         for (int q = 0; q < NO; ++q) {
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(1024) k_dir_prep(EvalPlan P, int n) {
     }
 }
 
-// Hybrid transforms: the directions of an orthant are also ordered by M = sum_k |xi_k|
+// Hybrid transforms: directions are grouped by the representative of their orthant's
+// pair (orthant and partner share a Delta table), and within a group ordered by M = sum_k |xi_k|
 // (ties by direction id), so that a tile of 32 DL consecutive directions spans a narrow
 // range of |<xi, v>| and its polynomial degree (chosen per tile from the largest M) stays
 // low.  One block per direction set sorts the keys
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(1024) k_dir_sort(EvalPlan P, int n) {
             const double* xi = dirs + (long long)d * n;
             double m = 0.0;
             for (int c = 0; c < n; ++c) m += fabs(xi[c]);
-            const int o = orthant_of(xi, n);
+            const int o = dir_group(xi, n, P.mode);
             atomicAdd(&cnt[o], 1);
             k = ((unsigned long long)o << 60) | ((unsigned long long)__float_as_uint((float)m) << 28) |
                 (unsigned long long)d;
