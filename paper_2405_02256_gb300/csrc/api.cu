@@ -970,6 +970,9 @@ topot_status slab_sum_f64(const double* d_parts, int P, int64_t n, double* d_out
 
 namespace topot {
 cudaError_t launch_exact(int n, bool u8, ExactArgs a, long long max_n, int sm_count, cudaStream_t st);
+int exact_radix_tile();
+constexpr int kExactProdLimit = 12288;   // staged coordinate products (96 KB of shared memory)
+size_t exact_keys_smem(int prod_max);
 cudaError_t launch_ect_exact_eval(int nseg, long long cap, const double* T, const int32_t* E, const long long* len,
                                   const double* t, int Q, int32_t* out, int sm_count, cudaStream_t st);
 cudaError_t launch_radon_exact_eval(int nseg, long long cap, const double* Tl, const int32_t* El,
@@ -1006,7 +1009,22 @@ topot_status exact_representation(const topot_tables* tc, int kind, const double
         return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: cap " + std::to_string(cap) +
                                                " < largest table " + std::to_string(max_n));
     const size_t slots = (size_t)nseg * (size_t)cap;
-    const size_t need = 2 * slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * (size_t)nseg + 8 * 256;
+    // radix tiles per segment; with more than one, per-segment digit counts and look-back words
+    const long long tile = exact_radix_tile();
+    const long long tps = std::max(1ll, (max_n + tile - 1) / tile);
+    if (nseg * tps > (1ll << 31) - 1)
+        return fail(TOPOT_ERR_INVALID_ARG, "exact_representation: too many radix tiles");
+    const size_t hist_n = tps > 1 ? (size_t)nseg * 8 * 256 : 0;
+    const size_t status_n = tps > 1 ? (size_t)(nseg * tps) * 256 : 0;
+    // per-direction coordinate products staged in shared memory when sum_k m_k fits
+    int prod_max = 0;
+    for (int b = 0; b < t->B; ++b) {
+        int sm = 0;
+        for (int k = 0; k < t->n; ++k) sm += t->h_img[b].m[k];
+        if (sm <= kExactProdLimit) prod_max = std::max(prod_max, sm);
+    }
+    const size_t need = 2 * slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * (size_t)nseg +
+                        sizeof(unsigned) * hist_n + sizeof(unsigned long long) * status_n + 9 * 256;
     topot_status s = ensure_ws(t, kWsExact, need);
     if (s != TOPOT_OK) return s;
     Carver cv{reinterpret_cast<char*>(t->ws[kWsExact])};
@@ -1023,11 +1041,19 @@ topot_status exact_representation(const topot_tables* tc, int kind, const double
     a.val[0] = cv.take<int>(slots);
     a.val[1] = cv.take<int>(slots);
     a.cnt = cv.take<int>((size_t)nseg);
+    a.tps = (int)tps;
+    a.prod_max = prod_max;
+    a.hist = hist_n ? cv.take<unsigned>(hist_n) : nullptr;
+    a.status = status_n ? cv.take<unsigned long long>(status_n) : nullptr;
+    a.tile_ctr = cv.take<int>(16);
     a.T = d_T;
     a.E = d_E;
     a.len = reinterpret_cast<long long*>(d_len);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     TOPOT_CUDA(cudaMemsetAsync(d_len, 0, sizeof(int64_t) * (size_t)nseg, st));
+    TOPOT_CUDA(cudaMemsetAsync(a.tile_ctr, 0, sizeof(int) * 16, st));
+    if (hist_n) TOPOT_CUDA(cudaMemsetAsync(a.hist, 0, sizeof(unsigned) * hist_n, st));
+    if (status_n) TOPOT_CUDA(cudaMemsetAsync(a.status, 0, sizeof(unsigned long long) * status_n, st));
     TOPOT_CUDA(launch_exact(t->n, t->dtype == TOPOT_U8, a, max_n, t->sm_count, st));
     return TOPOT_OK;
 }

@@ -127,6 +127,11 @@ struct ExactArgs {
     unsigned long long* key[2];      // [nseg][cap], ping-pong
     int* val[2];
     int* cnt;                        // [nseg] entries per segment
+    int tps;                         // radix tiles per segment (from the largest segment)
+    int prod_max;                    // coordinate products staged per direction (0: none)
+    unsigned* hist;                  // [nseg][8][256] digit counts (tps > 1), else null
+    unsigned long long* status;      // [nseg * tps][256] look-back words (tps > 1), zeroed per call
+    int* tile_ctr;                   // [16] tile tickets: the eight passes, then the finish
     double* T;                       // [nseg][cap]
     int32_t* E;
     long long* len;                  // [nseg]

@@ -35,11 +35,13 @@ IMAGES = {
     "example4x4": _example(),
     "bern64": synth.bernoulli((64, 64), 0.5, seed=0),
     "grf150x211": synth.grf((150, 211), 6.0, seed=1),
-    "grf512": synth.grf((512, 512), 8.0, seed=2),             # tables of ~3e4 points: merge passes
+    "grf512": synth.grf((512, 512), 8.0, seed=2),             # tables of ~3e4 points: several radix tiles
     "const": np.full((33, 17), 7, dtype=np.uint8),
     "i32_2d": np.random.default_rng(5).integers(-1000, 1000, size=(50, 70)).astype(np.int32),
     "grf20x33x40": synth.grf((20, 33, 40), 4.0, seed=7),
     "bin40x40x48": synth.grf((40, 40, 48), 5.0, seed=8, binary=True),
+    # sum of the sides above the staged coordinate products (12288): keys from divisions
+    "grf3x13000": synth.grf((3, 13000), 3.0, seed=10),
 }
 
 
@@ -118,3 +120,26 @@ def test_exact_cap_too_small(tb):
     d = torch.from_numpy(_dirs(2)).cuda()
     with pytest.raises(tb.TopotError):
         tb.exact_representation(tabs, 0, d, cap=3)
+
+
+def test_exact_full_size_2048(tb):
+    """Tables of a 2048^2 GRF image (about 4e5 points per table, a hundred radix tiles per
+    segment joined by look-back), two images sharing 5 directions (one axis-aligned,
+    one with a zero coordinate): both representations bit-exact."""
+    imgs = [synth.grf((2048, 2048), 16.0, seed=20), synth.grf((2048, 2048), 16.0, seed=21)]
+    tabs = tb.build_critical_tables(tb.pack_images(imgs))
+    dirs = np.concatenate([synth.random_2d_dirs(3, 22, 0.01, 1.0), np.array([[0.0, -1.0], [0.7, 0.0]])])
+    d = torch.from_numpy(dirs).cuda()
+    rep0 = tb.exact_representation(tabs, 0, d)
+    rep1 = tb.exact_representation(tabs, 1, d)
+    for b, img in enumerate(imgs):
+        ref = O.critical_tables(img)
+        for di, xi in enumerate(dirs):
+            T, E = rep0.segment(b, di)
+            Tw, Ew = O.ect_exact(ref, xi)
+            np.testing.assert_array_equal(T, Tw)
+            np.testing.assert_array_equal(E, Ew)
+            T, E = rep1.segment(b, di)
+            Tw, Ew = O.radon_exact(ref, xi)
+            np.testing.assert_array_equal(T, Tw)
+            np.testing.assert_array_equal(E, Ew)
