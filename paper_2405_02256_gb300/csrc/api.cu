@@ -24,10 +24,12 @@ cudaError_t launch_slab_sum_f64(const double* parts, int P, long long n, double*
                                 cudaStream_t st);
 cudaError_t launch_top_prepass(const void* pixels, topot_dtype dtype, int32_t* V, const TopSrc* src, int B, int n,
                                long long max_nv, int sm_count, cudaStream_t st);
+cudaError_t launch_top_prepass_u8(const uint8_t* pixels, uint8_t* V, const TopSrc* src, int B, int n, int sm_count,
+                                  cudaStream_t st);
 int extract_block(int n);
 int extract_k(int n);
 size_t extract_smem_bytes(int n, int elem_bytes, int row_stride, int stage_rows);
-cudaError_t launch_extract_u8(int n, const ExtractArgs& a, cudaStream_t st);
+cudaError_t launch_extract_u8(int n, bool top, const ExtractArgs& a, cudaStream_t st);
 cudaError_t launch_selftest_wait(int which, unsigned long long limit_ns, unsigned long long* flag, unsigned* err,
                                  cudaStream_t st);
 int extract_u8_threads(int n);
@@ -64,13 +66,14 @@ struct topot_tables {
     long long total_entries = 0;
     long long num_tiles = 0;
     int row_stride = 0, stage_rows = 0;
-    bool u8 = false;          // 8-bit batch, vertex construction: extraction by k_extract_u8
+    bool u8 = false;          // 8-bit batch: extraction by k_extract_u8 (either construction)
     int stage_bytes = 0;      // its staged bytes per tile (max over images)
-    bool top = false;         // top-dimensional construction: corner image, then k_extract
+    bool top = false;         // top-dimensional construction: corner image, then extraction
+                              // (k_extract_u8 on a u8 corner image, k_extract on an int32 one)
     bool gen = false;         // n = 4: the generic-n kernels (generic.cu) for every step
-    void* top_buf = nullptr;  // TopSrc[B] followed by the int32 corner images
+    void* top_buf = nullptr;  // TopSrc[B] followed by the corner images (u8 or int32)
     TopSrc* d_top = nullptr;
-    int32_t* d_corner = nullptr;
+    void* d_corner = nullptr;
     long long max_nv = 0;     // largest corner image (elements)
     // device memory
     void* meta = nullptr;             // one block: img, seg_count, chi, absum, err, ticket, status
@@ -220,15 +223,16 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         return cuda_fail(e, "tables_create: device query");
     }
     const bool top = construction == TOPOT_TOP;
-    // the top construction extracts from an int32 corner image (m_k + 1 per axis)
-    const int elem = (dtype == TOPOT_U8 && !top) ? 1 : 4;
+    // the top construction extracts from a corner image (m_k + 1 per axis): u8 with padded
+    // rows for 8-bit pixels, int32 otherwise
+    const int elem = dtype == TOPOT_U8 ? 1 : 4;
     const int pad = 16 / elem;
     const int tile_v = extract_block(n) * extract_k(n);
     const int NP = n == 3 ? 3 : 1;
     const size_t smem_budget = 96 * 1024;
     t->top = top;
     t->gen = n == 4;                      // generic-n kernels for every step
-    t->u8 = dtype == TOPOT_U8 && !top && !t->gen;
+    t->u8 = dtype == TOPOT_U8 && !t->gen;
     std::vector<TopSrc> h_top(top ? B : 0);
     long long v_elems = 0;
     long long tiles = 0, entries = 0;
@@ -270,12 +274,24 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
             I.nz = (int)(z1 - z0);
             N = (long long)I.m[0] * I.m[1] * I.nz;   // owned vertices: the capacity of a table
         }
+        long long top_q = 0;   // u8 corner image: positions (rows padded to top_pitch)
         if (top) {
-            // corner images start at multiples of 4 elements (16 bytes)
+            // corner images start at 16-byte boundaries
             h_top[b].pix_offset = h_offsets[b];
             h_top[b].v_offset = v_elems;
             I.offset = v_elems;
-            v_elems += (N + 3) & ~3ll;
+            if (t->u8) {
+                I.top_pitch = (int)align_up((size_t)I.m[0], 16);
+                top_q = (long long)I.top_pitch * I.m[1] * I.m[2];
+                if (top_q >= (1ll << 31)) {
+                    delete t;
+                    return fail(TOPOT_ERR_INVALID_ARG, "tables_create: corner image of >= 2^31 bytes");
+                }
+                h_top[b].pitch = I.top_pitch;
+                v_elems += top_q;
+            } else {
+                v_elems += (N + 3) & ~3ll;
+            }
             t->max_nv = std::max(t->max_nv, N);
         } else {
             I.offset = h_offsets[b];
@@ -290,7 +306,20 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
             tiles += (N + gen_block() - 1) / gen_block();
             continue;
         }
-        if (t->u8) {
+        if (t->u8 && top) {
+            // runs of `cap` positions of the corner image (rows and planes at fixed offsets);
+            // one staged run per offset of the 2^n pixels around a corner
+            const int cap = extract_u8_strip(n) * extract_u8_threads(n);
+            I.W = cap;
+            I.R = 1;
+            I.spr = extract_u8_threads(n);
+            I.rs = cap + 16;
+            I.nz = 1;
+            I.div_pitch = make_fastdiv((uint32_t)I.top_pitch);
+            t->stage_bytes = std::max(t->stage_bytes, (n == 3 ? 4 : 2) * I.rs + 32);
+            I.segs_per_row = 1;
+            I.tiles_per_plane = (int)((top_q + cap - 1) / cap);
+        } else if (t->u8) {
             // strips of `strip` vertices, one per thread; R full rows or one piece of a row
             const int strip = extract_u8_strip(n), threads = extract_u8_threads(n);
             I.W = std::min(m0, threads * strip);
@@ -310,8 +339,10 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
             I.W = tile_v;
             I.R = 1;
         }
-        I.segs_per_row = (m0 + I.W - 1) / I.W;
-        I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
+        if (!(t->u8 && top)) {
+            I.segs_per_row = (m0 + I.W - 1) / I.W;
+            I.tiles_per_plane = ((m1 + I.R - 1) / I.R) * I.segs_per_row;
+        }
         tiles += (long long)I.tiles_per_plane * I.nz;
         I.div0 = make_fastdiv((uint32_t)m0);
         I.div1 = make_fastdiv((uint32_t)m1);
@@ -363,13 +394,13 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
     t->clear_bytes = meta_bytes - o_chi;
     if (top) {
         const size_t src_bytes = align_up(sizeof(TopSrc) * B, 256);
-        e = cudaMalloc(&t->top_buf, src_bytes + sizeof(int32_t) * (size_t)v_elems);
+        e = cudaMalloc(&t->top_buf, src_bytes + (size_t)elem * (size_t)v_elems);
         if (e != cudaSuccess) {
             free_tables(t);
             return cuda_fail(e, "tables_create: corner image allocation");
         }
         t->d_top = reinterpret_cast<TopSrc*>(t->top_buf);
-        t->d_corner = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(t->top_buf) + src_bytes);
+        t->d_corner = reinterpret_cast<char*>(t->top_buf) + src_bytes;
         e = cudaMemcpy(t->d_top, h_top.data(), sizeof(TopSrc) * B, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_tables(t);
@@ -424,13 +455,19 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
         // per-block counts live in the look-back status words (tiles x S entries)
         TOPOT_CUDA(launch_extract_gen(t->dev(), t->dtype, d_pixels, t->num_tiles,
                                       reinterpret_cast<long long*>(t->status), st));
+    } else if (t->top && t->u8) {
+        TOPOT_CUDA(launch_top_prepass_u8(reinterpret_cast<const uint8_t*>(d_pixels),
+                                         reinterpret_cast<uint8_t*>(t->d_corner), t->d_top, t->B, t->n, t->sm_count,
+                                         st));
+        a.pixels = t->d_corner;
+        TOPOT_CUDA(launch_extract_u8(t->n, true, a, st));
     } else if (t->top) {
-        TOPOT_CUDA(launch_top_prepass(d_pixels, t->dtype, t->d_corner, t->d_top, t->B, t->n, t->max_nv, t->sm_count,
-                                      st));
+        TOPOT_CUDA(launch_top_prepass(d_pixels, t->dtype, reinterpret_cast<int32_t*>(t->d_corner), t->d_top, t->B,
+                                      t->n, t->max_nv, t->sm_count, st));
         a.pixels = t->d_corner;
         TOPOT_CUDA(launch_extract(t->n, t->dtype, true, a, st));
     } else if (t->u8) {
-        TOPOT_CUDA(launch_extract_u8(t->n, a, st));
+        TOPOT_CUDA(launch_extract_u8(t->n, false, a, st));
     } else {
         TOPOT_CUDA(launch_extract(t->n, t->dtype, false, a, st));
     }

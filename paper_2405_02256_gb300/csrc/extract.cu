@@ -129,6 +129,39 @@ __global__ void k_top_prepass(const Tpix* __restrict__ pix, int32_t* __restrict_
     }
 }
 
+// u8 corner image of the top-dimensional construction of an 8-bit image: V(v) =
+// pixel(v - 1) when every v_k >= 1, else 255; rows padded to `pitch` bytes with 255.
+// 255 stands for "no pixel": it is at least every pixel, so a box with some pixels takes
+// their minimum, and boxes with none take 255 together and cancel in the alternating
+// sum of the lower star -- except at the 2^n corners of the image, which the extraction
+// corrects (k_extract_u8).  Blocks over corner-image rows, four bytes per thread.
+__global__ void k_top_prepass_u8(const uint8_t* __restrict__ pix, uint8_t* __restrict__ V,
+                                 const TopSrc* __restrict__ src, int B, int n) {
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const TopSrc s = src[b];
+        const int M1 = s.m[1] + 1, M2 = n == 3 ? s.m[2] + 1 : 1;
+        const int words = s.pitch >> 2;
+        const uint8_t* pb = pix + s.pix_offset;
+        uint32_t* vb = reinterpret_cast<uint32_t*>(V + s.v_offset);
+        for (int row = blockIdx.x; row < M1 * M2; row += gridDim.x) {
+            const int z = row / M1, y = row - z * M1;
+            const bool inside = y >= 1 && (n == 2 || z >= 1);
+            // pixel row (z - 1, y - 1); column x of the corner image is pixel x - 1
+            const long long prow = ((long long)(n == 3 ? z - 1 : 0) * s.m[1] + (y - 1)) * s.m[0];
+            for (int w = threadIdx.x; w < words; w += blockDim.x) {
+                uint32_t v = 0u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = 4 * w + k;
+                    const uint32_t px = (inside && x >= 1 && x <= s.m[0]) ? (uint32_t)pb[prow + x - 1] : 255u;
+                    v |= px << (8 * k);
+                }
+                vb[(long long)row * words + w] = v;
+            }
+        }
+    }
+}
+
 template <int NDIM, typename Tin, typename Tval, int BLOCK, int K, bool TOP>
 __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     using PT = PixTraits<Tin>;
@@ -455,6 +488,14 @@ cudaError_t launch_top_prepass(const void* pixels, topot_dtype dtype, int32_t* V
         k_top_prepass<uint8_t><<<grid, 256, 0, st>>>(reinterpret_cast<const uint8_t*>(pixels), V, src, B, n);
     else
         k_top_prepass<int32_t><<<grid, 256, 0, st>>>(reinterpret_cast<const int32_t*>(pixels), V, src, B, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_top_prepass_u8(const uint8_t* pixels, uint8_t* V, const TopSrc* src, int B, int n, int sm_count,
+                                  cudaStream_t st) {
+    const int gy = std::min(B, 65535);
+    const int gx = std::max(1, std::min(65535, 8 * sm_count / gy + 1));
+    k_top_prepass_u8<<<dim3(gx, gy), 256, 0, st>>>(pixels, V, src, B, n);
     return cudaGetLastError();
 }
 

@@ -217,6 +217,124 @@ __device__ __forceinline__ void strip_values3(const uint8_t* sp, int rs, int ps,
         for (int p = 0; p < 2; ++p) D[8 + r][p] = hsub2(D[r][p], D[r ^ 7][p]);
 }
 
+// Top-dimensional construction (Section 4.1), corner v with the 2^n pixels X_g = V(v + g),
+// g in {0,1}^n, of the u8 corner image V.  The lower-star box of orthant o spanning the
+// axes delta takes the minimum t_delta over the pixels with g_k = o_k on those axes, and
+//   Delta^-_o(v) = sum_delta (-1)^|delta| t_delta,
+// grouped (2-D) as (t_0 - t_x) + (t_xy - t_y) and (3-D) as (t_0 - t_x) + (t_xy - t_y)
+// + (t_xz - t_z) + (t_yz - t_xyz): each bracket is a difference of a minimum and a
+// minimum over a superset or subset of its pixels, of magnitude <= 255, so every partial
+// sum is an exact half-precision integer.
+
+// One staged run of the corner image: P[p] = (X[2p], X[2p+1]), S[p] = (X[2p+1], X[2p+2]);
+// sp[2 PAIRS] (the next position) is always staged.
+template <int PAIRS>
+__device__ __forceinline__ void run_pairs(const uint8_t* sp, uint32_t (&P)[PAIRS], uint32_t (&S)[PAIRS]) {
+    constexpr uint32_t K = 0x64646464u;
+    uint32_t w[2];
+    if constexpr (PAIRS == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(sp);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
+        w[0] = *reinterpret_cast<const uint32_t*>(sp);
+        w[1] = 0;
+    }
+    const uint32_t h = sp[2 * PAIRS];
+#pragma unroll
+    for (int p = 0; p < PAIRS; ++p) P[p] = __byte_perm(w[p >> 1], K, (p & 1) ? 0x4342 : 0x4140);
+#pragma unroll
+    for (int p = 0; p + 1 < PAIRS; ++p) S[p] = __byte_perm(P[p], P[p + 1], 0x5432);
+    S[PAIRS - 1] = __byte_perm(P[PAIRS - 1], h, 0x3432);
+}
+
+// 2-D: s0 the run of row y, s1 of row y + 1.  D[o] (o < 4) lower tables, D[4 + r] =
+// D[r] - D[r ^ 3].
+__device__ __forceinline__ void strip_values_top2(const uint8_t* s0, const uint8_t* s1, uint32_t (&D)[6][4]) {
+    uint32_t X0[4], X1[4], Y0[4], Y1[4];      // X_{gx gy}: (g_x, g_y) = (0,0), (1,0); (0,1), (1,1)
+    run_pairs<4>(s0, X0, X1);
+    run_pairs<4>(s1, Y0, Y1);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t cm0 = hmin2(X0[p], Y0[p]), cm1 = hmin2(X1[p], Y1[p]);   // t_x: g_x = 0, 1
+        const uint32_t rm0 = hmin2(X0[p], X1[p]), rm1 = hmin2(Y0[p], Y1[p]);   // t_y: g_y = 0, 1
+        const uint32_t t0 = hmin2(cm0, cm1);
+        const uint32_t a0 = hsub2(t0, cm0), a1 = hsub2(t0, cm1);
+        D[0][p] = hadd2(a0, hsub2(X0[p], rm0));
+        D[1][p] = hadd2(a1, hsub2(X1[p], rm0));
+        D[2][p] = hadd2(a0, hsub2(Y0[p], rm1));
+        D[3][p] = hadd2(a1, hsub2(Y1[p], rm1));
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        D[4][p] = hsub2(D[0][p], D[3][p]);
+        D[5][p] = hsub2(D[1][p], D[2][p]);
+    }
+}
+
+// 3-D: sr[2 g_z + g_y] the run of row y + g_y of plane z + g_z.  D[o] (o < 8) lower
+// tables, D[8 + r] = D[r] - D[r ^ 7].
+__device__ __forceinline__ void strip_values_top3(const uint8_t* const (&sr)[4], uint32_t (&D)[12][2]) {
+    uint32_t X[2][2][2][2];                   // [g_z][g_y][g_x][pair]
+#pragma unroll
+    for (int gz = 0; gz < 2; ++gz)
+#pragma unroll
+        for (int gy = 0; gy < 2; ++gy) run_pairs<2>(sr[2 * gz + gy], X[gz][gy][0], X[gz][gy][1]);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        uint32_t txy[2][2], txz[2][2], tyz[2][2], tx[2], ty[2], tz[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                txy[a][c] = hmin2(X[0][a][c][p], X[1][a][c][p]);   // [g_y][g_x]
+                txz[a][c] = hmin2(X[a][0][c][p], X[a][1][c][p]);   // [g_z][g_x]
+                tyz[a][c] = hmin2(X[a][c][0][p], X[a][c][1][p]);   // [g_z][g_y]
+            }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            tx[a] = hmin2(txy[0][a], txy[1][a]);
+            ty[a] = hmin2(txy[a][0], txy[a][1]);
+            tz[a] = hmin2(txz[a][0], txz[a][1]);
+        }
+        const uint32_t t0 = hmin2(tx[0], tx[1]);
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+            const uint32_t u = hadd2(hsub2(t0, tx[ox]), hsub2(txy[oy][ox], ty[oy]));
+            const uint32_t w = hadd2(hsub2(txz[oz][ox], tz[oz]), hsub2(tyz[oz][oy], X[oz][oy][ox][p]));
+            D[o][p] = hadd2(u, w);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) D[8 + r][p] = hsub2(D[r][p], D[r ^ 7][p]);
+}
+
+// Corners of the image (every coordinate 0 or m_k - 1) in the orthant pointing out of
+// the image on every axis: every box but the vertex itself has no pixel, and those 255s
+// sum to -255 instead of 0.  Adds 255 there and recomputes the Delta tables.
+template <int NDIM, int SEG, int PAIRS>
+__device__ __forceinline__ void top_corner_fix(uint32_t (&D)[SEG][PAIRS], int xs, int m0, bool ylast, bool zlast) {
+    constexpr int NO = 1 << NDIM;
+#pragma unroll
+    for (int k = 0; k < 2 * PAIRS; ++k) {
+        const int x = xs + k;
+        if (x == 0 || x == m0 - 1) {
+            const int ob = (x == m0 - 1 ? 1 : 0) | (ylast ? 2 : 0) | (zlast ? 4 : 0);
+            const uint32_t add = (k & 1) ? 0x5BF80000u : 0x00005BF8u;   // 255.0 in the vertex's half
+#pragma unroll
+            for (int o = 0; o < NO; ++o)
+                if (o == ob) D[o][k >> 1] = hadd2(D[o][k >> 1], add);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NO / 2; ++r)
+#pragma unroll
+        for (int p = 0; p < PAIRS; ++p) D[NO + r][p] = hsub2(D[r][p], D[r ^ (NO - 1)][p]);
+}
+
 // number of non-zero halves of the pairs
 template <int PAIRS>
 __device__ __forceinline__ uint32_t count_nonzero(const uint32_t (&d)[PAIRS]) {
@@ -267,7 +385,7 @@ struct TileGeo {
     const uint8_t* img;
 };
 
-template <int NDIM>
+template <int NDIM, bool TOP>
 __device__ __forceinline__ TileGeo tile_geometry(const ExtractArgs& p, int b, long long ticket) {
     const ImgDesc* Ip = p.t.img + b;
     TileGeo g;
@@ -283,6 +401,17 @@ __device__ __forceinline__ TileGeo tile_geometry(const ExtractArgs& p, int b, lo
     g.packed = __ldg(&Ip->packed);
     g.tile_begin = __ldg(&Ip->tile_begin);
     g.lt = (int)(ticket - g.tile_begin);
+    if (TOP) {   // a run of positions of the corner image
+        const long long Q = (long long)__ldg(&Ip->top_pitch) * g.m1 * g.m2;
+        g.z = 0;
+        g.nz = 1;
+        g.y0 = 0;
+        g.x0 = g.lt * g.W;
+        g.rows = 1;
+        g.cols = (int)min((long long)g.W, Q - g.x0);
+        g.img = reinterpret_cast<const uint8_t*>(p.pixels) + __ldg(&Ip->offset);
+        return g;
+    }
     const int zl = NDIM == 3 ? (int)fastdiv((uint32_t)g.lt, ldg_fastdiv(&Ip->div_tpp)) : 0;   // owned plane
     g.z = NDIM == 3 ? __ldg(&Ip->zlo) + zl : 0;                                            // volume plane
     g.nz = NDIM == 3 ? __ldg(&Ip->nz) : 1;
@@ -348,7 +477,34 @@ __device__ __forceinline__ void issue_stage_copies(const TileGeo& g, uint8_t* st
     }
 }
 
+// Top construction: the tile's run and the runs at the offsets of the other pixels of a
+// corner (+pitch; in 3-D +plane, +plane+pitch), each W + 16 bytes (the last position reads
+// one beyond), clipped at the end of the corner image (the block fills the rest with 255).
 template <int NDIM>
+__device__ __forceinline__ int top_run_len(const TileGeo& g, int P, int k) {
+    const long long plane = (long long)P * g.m1;
+    const long long Q = plane * g.m2;
+    const long long start = g.x0 + (k & 1) * (long long)P + (k >> 1) * plane;
+    return (int)max(0ll, min((long long)g.RS, Q - start));
+}
+
+template <int NDIM>
+__device__ __forceinline__ void issue_top_copies(const TileGeo& g, int P, uint8_t* stage, uint64_t* bar) {
+    constexpr int kNB = NDIM == 3 ? 4 : 2;
+    const long long plane = (long long)P * g.m1;
+    unsigned bytes = 0;
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) bytes += (unsigned)top_run_len<NDIM>(g, P, k);
+    mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+    for (int k = 0; k < kNB; ++k) {
+        const int len = top_run_len<NDIM>(g, P, k);
+        if (len > 0)
+            bulk_g2s(stage + k * g.RS, g.img + g.x0 + (k & 1) * (long long)P + (k >> 1) * plane, (unsigned)len, bar);
+    }
+}
+
+template <int NDIM, bool TOP>
 __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u8(ExtractArgs p) {
     using Ly = U8Layout<NDIM>;
     constexpr int kB = Ly::B, kNW = Ly::NW, kSeg = Ly::SEG, kNO = Ly::NO;
@@ -382,14 +538,16 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
         sh_int[0] = (int)ticket;
         sh_int[1] = lo;
         // the tile's bulk copies go out before the block synchronises
-        issue_stage_copies<NDIM>(tile_geometry<NDIM>(p, lo, ticket), stage, bar);
+        const TileGeo g0 = tile_geometry<NDIM, TOP>(p, lo, ticket);
+        if (TOP) issue_top_copies<NDIM>(g0, __ldg(&T.img[lo].top_pitch), stage, bar);
+        else issue_stage_copies<NDIM>(g0, stage, bar);
     }
     __syncthreads();
 
     const long long ticket = (unsigned)sh_int[0];
     const int b = sh_int[1];
     const ImgDesc* Ip = T.img + b;
-    const TileGeo G = tile_geometry<NDIM>(p, b, ticket);
+    const TileGeo G = tile_geometry<NDIM, TOP>(p, b, ticket);
     const int m0 = G.m0, m1 = G.m1, m2 = G.m2, R = G.R, spr = G.spr, RS = G.RS, tpp = G.tpp;
     const long long tile_begin = G.tile_begin;
     const int lt = G.lt, z = G.z, y0 = G.y0, x0 = G.x0, rows = G.rows, cols = G.cols;
@@ -405,7 +563,16 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     const int srows = rows + 2;
     const int PS = (R + 2) * RS;                       // staged plane stride
     const bool packed = __ldg(&Ip->packed) != 0;
-    if (packed) {
+    if (TOP) {
+        // the clipped ends of the runs: 255 (no pixel)
+        const int P = __ldg(&Ip->top_pitch);
+#pragma unroll
+        for (int k = 0; k < (NDIM == 3 ? 4 : 2); ++k) {
+            const int len = top_run_len<NDIM>(G, P, k);
+            uint4* dst = reinterpret_cast<uint4*>(stage + k * RS);
+            for (int c = (len >> 4) + tid; c < (RS >> 4); c += kB) dst[c] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+    } else if (packed) {
         // bulk copies need a 16-byte aligned source: the pixel buffer itself may not be
         const bool bulk = (reinterpret_cast<uintptr_t>(img) & 15) == 0;
         if (!bulk) {
@@ -467,10 +634,34 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     const int g = tid - r * spr;
     uint32_t D[kSeg][kPairs];
     if (r < rows) {
-        const uint8_t* sp = stage + (NDIM == 3 ? PS : 0) + r * RS + kPadB + kStrip * g;
-        const bool hasL = !packed || g > 0, hasR = !packed || g < spr - 1;
-        if constexpr (NDIM == 2) strip_values2(sp, RS, hasL, hasR, D);
-        else strip_values3(sp, RS, PS, hasL, hasR, D);
+        if constexpr (TOP) {
+            // positions past the end of the corner image read 255 everywhere: all zero
+            const uint8_t* s0 = stage + kStrip * g;
+            if constexpr (NDIM == 2) {
+                strip_values_top2(s0, s0 + RS, D);
+            } else {
+                const uint8_t* const sr[4] = {s0, s0 + RS, s0 + 2 * RS, s0 + 3 * RS};
+                strip_values_top3(sr, D);
+            }
+            // the corners of the image: boxes with no pixel on every axis do not cancel
+            const int P = __ldg(&Ip->top_pitch);
+            const int q0 = x0 + kStrip * g;
+            const int yq = (int)fastdiv((uint32_t)q0, ldg_fastdiv(&Ip->div_pitch));   // z m_1 + y
+            const int xs = q0 - yq * P;
+            int yy = yq, zz = 0;
+            if (NDIM == 3) {
+                zz = (int)fastdiv((uint32_t)yq, ldg_fastdiv(&Ip->div1));
+                yy = yq - zz * m1;
+            }
+            if ((yy == 0 || yy == m1 - 1) && (NDIM == 2 || zz == 0 || zz == m2 - 1) &&
+                (xs == 0 || (xs <= m0 - 1 && m0 - 1 < xs + kStrip)))
+                top_corner_fix<NDIM>(D, xs, m0, yy == m1 - 1, NDIM == 3 && zz == m2 - 1);
+        } else {
+            const uint8_t* sp = stage + (NDIM == 3 ? PS : 0) + r * RS + kPadB + kStrip * g;
+            const bool hasL = !packed || g > 0, hasR = !packed || g < spr - 1;
+            if constexpr (NDIM == 2) strip_values2(sp, RS, hasL, hasR, D);
+            else strip_values3(sp, RS, PS, hasL, hasR, D);
+        }
     } else {
 #pragma unroll
         for (int s = 0; s < kSeg; ++s)
@@ -637,6 +828,8 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     int red[1 + kNO];
 #pragma unroll
     for (int i = 0; i <= kNO; ++i) red[i] = 0;
+    const FastDiv divp = TOP ? ldg_fastdiv(&Ip->div_pitch) : FastDiv{0u, 0u, 0u};
+    const int top_p = TOP ? __ldg(&Ip->top_pitch) : 0;
     {
         uint32_t base = 0, cum = 0;
 #pragma unroll
@@ -659,7 +852,13 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
                     if (e >= 0 && e < n) {
                         const uint32_t w = o[e];
                         v[k] = (int)__half2short_rn(__ushort_as_half((unsigned short)(w & 0xffffu)));
-                        id[k] = L0 + (int)(w >> 16);
+                        if constexpr (TOP) {   // position -> vertex index (rows m_0 long)
+                            const int q = x0 + (int)(w >> 16);
+                            const int yq = (int)fastdiv((uint32_t)q, divp);
+                            id[k] = yq * m0 + (q - yq * top_p);
+                        } else {
+                            id[k] = L0 + (int)(w >> 16);
+                        }
                     }
                     if (s < kNO) red[1 + (s < kNO ? s : 0)] += abs(v[k]);
                     if (s == 0) red[0] += v[k];
@@ -705,9 +904,9 @@ size_t extract_u8_smem_bytes(int n, int stage_bytes) {
     return (size_t)(n == 2 ? U8Layout<2>::OFF_STAGE : U8Layout<3>::OFF_STAGE) + (size_t)stage_bytes;
 }
 
-template <int NDIM>
+template <int NDIM, bool TOP>
 static cudaError_t launch_u8(const ExtractArgs& a, cudaStream_t st) {
-    auto kern = k_extract_u8<NDIM>;
+    auto kern = k_extract_u8<NDIM, TOP>;
     static cudaError_t attr = [&] {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e == cudaSuccess)
@@ -720,8 +919,9 @@ static cudaError_t launch_u8(const ExtractArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_extract_u8(int n, const ExtractArgs& a, cudaStream_t st) {
-    return n == 2 ? launch_u8<2>(a, st) : launch_u8<3>(a, st);
+cudaError_t launch_extract_u8(int n, bool top, const ExtractArgs& a, cudaStream_t st) {
+    if (top) return n == 2 ? launch_u8<2, true>(a, st) : launch_u8<3, true>(a, st);
+    return n == 2 ? launch_u8<2, false>(a, st) : launch_u8<3, false>(a, st);
 }
 
 }  // namespace topot

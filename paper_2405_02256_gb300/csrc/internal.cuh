@@ -78,6 +78,11 @@ struct ImgDesc {
     int zlo;
     int zbase;
     int nz;
+    // top-dimensional construction of an 8-bit image: the corner image is a u8 array with
+    // rows top_pitch bytes apart (a multiple of 16, >= m_0), planes top_pitch * m_1 apart;
+    // extraction tiles are runs of positions of that array.  0 for every other image.
+    int top_pitch;
+    FastDiv div_pitch;      // division by top_pitch
 };
 
 // Device view of a tables handle.
@@ -113,6 +118,7 @@ struct TopSrc {
     long long pix_offset;   // element offset of the pixels in the caller's buffer
     long long v_offset;     // element offset of the corner image in the handle's buffer
     int m[3];               // pixels per axis (m_2 = 1 for n = 2)
+    int pitch;              // u8 corner image: row pitch (bytes); 0: int32 corner image, rows m_0 + 1
 };
 
 // Arguments of the exact-representation kernels (one segment per image and direction).

@@ -33,6 +33,14 @@ IMAGES = {
     "bern9x10x11": synth.bernoulli((9, 10, 11), 0.5, seed=6),
     "grf20x33x40": synth.grf((20, 33, 40), 4.0, seed=7),
     "i32_3d": np.random.default_rng(6).integers(-50, 50, size=(8, 9, 10)).astype(np.int32),
+    # 8-bit images take a u8 corner image where 255 also stands for "no pixel"
+    "all255_7x9": np.full((7, 9), 255, dtype=np.uint8),
+    "border255_31x47": np.pad(synth.uniform_u8((29, 45), seed=8), 1, constant_values=255),
+    "corners255_16x16": np.where(np.outer(np.arange(16) % 15 == 0, np.arange(16) % 15 == 0), 255,
+                                 synth.uniform_u8((16, 16), seed=9)).astype(np.uint8),
+    "bin0_255_6x7x8": (synth.bernoulli((6, 7, 8), 0.5, seed=10) * 255).astype(np.uint8),
+    "all255_3x4x5": np.full((3, 4, 5), 255, dtype=np.uint8),
+    "grf2x3x700": synth.grf((2, 3, 700), 3.0, seed=11),
 }
 
 
@@ -78,3 +86,11 @@ def test_top_ragged_batch(tb):
     tabs = tb.build_critical_tables(tb.pack_images(imgs, align=1), construction="top")
     for b, img in enumerate(imgs):
         _check(tabs, b, O.critical_tables(img, "top"))
+
+
+def test_top_full_size_2048(tb):
+    """A 2048^2 image (2049^2 corners, rows padded to 2064 bytes, runs of 4096 positions that
+    cross rows): tables bit-exact."""
+    img = synth.grf((2048, 2048), 16.0, seed=70)
+    tabs = tb.build_critical_tables(tb.pack_images([img]), construction="top")
+    _check(tabs, 0, O.critical_tables(img, "top"))
