@@ -134,29 +134,52 @@ __global__ void k_top_prepass(const Tpix* __restrict__ pix, int32_t* __restrict_
 // 255 stands for "no pixel": it is at least every pixel, so a box with some pixels takes
 // their minimum, and boxes with none take 255 together and cancel in the alternating
 // sum of the lower star -- except at the 2^n corners of the image, which the extraction
-// corrects (k_extract_u8).  Blocks over corner-image rows, four bytes per thread.
+// corrects (k_extract_u8).  Blocks over corner-image rows, 16 bytes per thread: from
+// 16-byte loads when the pixel row is 16-byte aligned (one byte from the previous chunk),
+// else byte by byte.
 __global__ void k_top_prepass_u8(const uint8_t* __restrict__ pix, uint8_t* __restrict__ V,
                                  const TopSrc* __restrict__ src, int B, int n) {
     for (int b = blockIdx.y; b < B; b += gridDim.y) {
         const TopSrc s = src[b];
         const int M1 = s.m[1] + 1, M2 = n == 3 ? s.m[2] + 1 : 1;
-        const int words = s.pitch >> 2;
+        const int chunks = s.pitch >> 4;
         const uint8_t* pb = pix + s.pix_offset;
-        uint32_t* vb = reinterpret_cast<uint32_t*>(V + s.v_offset);
+        uint4* vb = reinterpret_cast<uint4*>(V + s.v_offset);
         for (int row = blockIdx.x; row < M1 * M2; row += gridDim.x) {
             const int z = row / M1, y = row - z * M1;
             const bool inside = y >= 1 && (n == 2 || z >= 1);
             // pixel row (z - 1, y - 1); column x of the corner image is pixel x - 1
             const long long prow = ((long long)(n == 3 ? z - 1 : 0) * s.m[1] + (y - 1)) * s.m[0];
-            for (int w = threadIdx.x; w < words; w += blockDim.x) {
-                uint32_t v = 0u;
+            const uint8_t* pr = pb + (inside ? prow : 0);
+            const bool aligned = (reinterpret_cast<uintptr_t>(pr) & 15) == 0;
+            for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+                const int x0 = 16 * c;                    // corner columns x0 .. x0 + 15
+                uint32_t w[4];
+                if (!inside) {
+                    w[0] = w[1] = w[2] = w[3] = 0xffffffffu;
+                } else if (aligned && x0 + 16 <= s.m[0]) {
+                    // pixels x0 - 1 .. x0 + 14: the chunk x0 .. x0 + 15 (inside the row) shifted
+                    // up one byte
+                    const uint4 q = *reinterpret_cast<const uint4*>(pr + x0);
+                    const uint32_t prev = c > 0 ? (uint32_t)pr[x0 - 1] : 255u;
+                    w[0] = __byte_perm(prev, q.x, 0x6540);
+                    w[1] = __byte_perm(q.x, q.y, 0x6543);
+                    w[2] = __byte_perm(q.y, q.z, 0x6543);
+                    w[3] = __byte_perm(q.z, q.w, 0x6543);
+                } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int x = 4 * w + k;
-                    const uint32_t px = (inside && x >= 1 && x <= s.m[0]) ? (uint32_t)pb[prow + x - 1] : 255u;
-                    v |= px << (8 * k);
+                    for (int j = 0; j < 4; ++j) {
+                        uint32_t v = 0u;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int x = x0 + 4 * j + k;
+                            const uint32_t px = (x >= 1 && x <= s.m[0]) ? (uint32_t)pr[x - 1] : 255u;
+                            v |= px << (8 * k);
+                        }
+                        w[j] = v;
+                    }
                 }
-                vb[(long long)row * words + w] = v;
+                vb[(long long)row * chunks + c] = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
     }
