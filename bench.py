@@ -38,11 +38,11 @@ B_IMAGES, SIDE, ELL = 64, 2048, 16.0
 D_ECT, T_ECT, D_HT = 1024, 512, 4096
 KERNELS = ("laplace", "fourier", "bessel")
 FP64_SAMPLE_DIRS = 128
-# DRAM bytes (read + write) per image of one FP32C hybrid launch, from the ncu capture of
-# the 8-image case in profiles/k_ht_f32_8x2048_grf.md (the tables are read once per work
-# item, so the traffic grows with the number of images)
-HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.1e6 + 4.5e6) / 8, "ht_fourier": (92.1e6 + 4.9e6) / 8,
-                           "ht_bessel": (97.4e6 + 4.3e6) / 8}
+# DRAM bytes (read + write) per image of one FP32C hybrid launch: dram__bytes_read.sum +
+# dram__bytes_write.sum of the packed launches in an ncu capture of the 8-image case (the
+# tables are read once per work item, so the traffic grows with the number of images)
+HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.03e6 + 3.71e6) / 8, "ht_fourier": (85.90e6 + 1.19e6) / 8,
+                           "ht_bessel": (96.63e6 + 0.95e6) / 8}
 
 
 def bench_config(n_img: int, side: int, world: int) -> dict:
@@ -278,7 +278,11 @@ def run_gpu(args):
     # operation counts 2, MUFU operations are not counted; the average over the MUFU and
     # polynomial halves for Fourier), and issued instructions per (point, direction)
     # update of the ECT kernel; both counted from the kernel source
-    fp32_ops = {"ht_laplace": 3.5, "ht_fourier": 9.5, "ht_bessel": 8.5}
+    # (packed f32x2: argument 2, accumulation 1 per component, block-compensated sums about
+    # 0.6 per component; Fourier: the mean of a polynomial pair, 12.25, and a MUFU pair with
+    # the FMUL range reduction of sin and cos, 8.5; Bessel: 7.6 on the |z| <= 0.5 path that
+    # almost every tile of this direction law takes)
+    fp32_ops = {"ht_laplace": 3.6, "ht_fourier": 10.4, "ht_bessel": 7.6}
     # warp instructions per 32 (point, direction) updates of k_hist, from its ncu
     # capture (instructions executed / updates x 32)
     ect_instr = 23.0
@@ -371,6 +375,13 @@ def _sizes(tabs, n_img, NO):
     return nl, nd
 
 
+_ROWS = None   # names of the extra rows to run (None: all)
+
+
+def _want(name: str) -> bool:
+    return _ROWS is None or name in _ROWS
+
+
 def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_img, dev):
     """Every other row of the hot path, measured on its own workload."""
     import torch
@@ -379,94 +390,101 @@ def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_
     from paper_2405_02256_gb300 import synth
     rows = {}
     R2 = synth.image_radius(2)
-
-    # a6: Radon on the same 2048^2 tables, 1024 directions x 512 thresholds (two tables per direction)
-    out = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
-    ms = _time_cuda(lambda: tb.radon(tabs, dirs_ect, -R2, R2, T_ECT, out=out))
-    cnt = np.bincount(_orthants(dirs_ect_h), minlength=4)
-    upd = int(sum(cnt[o] * (nl[:, o] + nl[:, o ^ 3]).sum() for o in range(4)))
-    rows["radon_2d"] = {"workload": "same 64 x 2048^2 tables; 1024 dirs x 512 thresholds", "ms": ms,
-                        "dirs_per_s": n_img * D_ECT / (ms / 1e3), "updates_per_s": upd / (ms / 1e3)}
-
-    # a8: adjoint of Laplace and Fourier at the 4096 hybrid directions
+    # (point, direction) terms of one hybrid transform over the 4096 directions
     terms = int((nd * np.bincount(_orthants(dirs_ht_h), minlength=4)[None, :]).sum())
-    g = torch.empty_like(dirs_ht)
-    adj = {}
-    for k in ("laplace", "fourier"):
-        gout = torch.ones((n_img, D_HT, 2) if k == "fourier" else (n_img, D_HT), dtype=torch.float64, device=dev)
-        ms = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, dirs_ht, gout, "fp32c", out=g), reps=1)
-        adj[k] = {"ms": ms, "terms_per_s": terms / (ms / 1e3)}
-    rows["adjoint_2d"] = {"workload": "same tables; 4096 dirs, d/dxi of sum_b,d HT", **adj}
 
-    # f3: kappa = sin (the kernel of the paper's experiments)
-    o_sine = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
-    ms = _time_cuda(lambda: tb.hybrid_transform(tabs, "sine", dirs_ht, "fp32c", out=o_sine), reps=1)
-    rows["sine_2d"] = {"workload": "same tables; 4096 dirs, kappa = sin (kbar = -cos), FP32C",
-                       "ms": ms, "terms_per_s": terms / (ms / 1e3)}
-    del o_sine
+    if _want("radon_2d"):
+        # Radon on the same 2048^2 tables, 1024 directions x 512 thresholds (two tables per direction)
+        out = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
+        ms = _time_cuda(lambda: tb.radon(tabs, dirs_ect, -R2, R2, T_ECT, out=out))
+        cnt = np.bincount(_orthants(dirs_ect_h), minlength=4)
+        upd = int(sum(cnt[o] * (nl[:, o] + nl[:, o ^ 3]).sum() for o in range(4)))
+        rows["radon_2d"] = {"workload": "same 64 x 2048^2 tables; 1024 dirs x 512 thresholds", "ms": ms,
+                            "dirs_per_s": n_img * D_ECT / (ms / 1e3), "updates_per_s": upd / (ms / 1e3)}
 
-    # f3: a tabulated kernel, kbar given by K samples (piecewise linear, constant ends);
-    # here K = 1024 samples of sin(2 s) + 0.3 s^2 on [-R, R]
-    tab_rows = {}
-    for K in (64, 1024):
-        sk = -R2 + 2 * R2 / (K - 1) * np.arange(K)
-        kt = tb.KernelTable(np.sin(2.0 * sk) + 0.3 * sk * sk, -R2, R2)
-        o_tab = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
-        ms = _time_cuda(lambda: tb.hybrid_transform(tabs, kt, dirs_ht, "fp32c", out=o_tab), reps=1)
-        tab_rows[f"K{K}_ms"] = ms
-        tab_rows[f"K{K}_terms_per_s"] = terms / (ms / 1e3)
-        del o_tab
-        kt.free()
-    rows["table_2d"] = {"workload": "same tables; 4096 dirs, kbar tabulated by K samples on [-R, R], FP32C",
-                        **tab_rows}
+    if _want("adjoint_2d"):
+        # adjoint of Laplace and Fourier at the 4096 hybrid directions
+        g = torch.empty_like(dirs_ht)
+        adj = {}
+        for k in ("laplace", "fourier"):
+            gout = torch.ones((n_img, D_HT, 2) if k == "fourier" else (n_img, D_HT), dtype=torch.float64, device=dev)
+            ms = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, dirs_ht, gout, "fp32c", out=g), reps=1)
+            adj[k] = {"ms": ms, "terms_per_s": terms / (ms / 1e3)}
+        rows["adjoint_2d"] = {"workload": "same tables; 4096 dirs, d/dxi of sum_b,d HT", **adj}
 
-    # f1: exact representations (T, E) and (T', E') at 4 directions per image, and their
-    # evaluation at 4096 arbitrary thresholds
-    tabs.sync()                                   # sizes on the host (the step rebuilt the tables)
-    d4 = dirs_ht[:4].contiguous()
-    o4 = _orthants(dirs_ht_h[:4])
-    ent0 = int(sum(nl[:, o].sum() for o in o4))
-    ent1 = int(sum(nd[:, o if o < 2 else o ^ 3].sum() for o in o4))
-    cap0 = int(nl.max())
-    cap1 = int(nd.max())
-    reps = {}
-    ms0 = _time_cuda(lambda: reps.__setitem__(0, tb.exact_representation(tabs, 0, d4, cap=cap0)), reps=2)
-    ms1 = _time_cuda(lambda: reps.__setitem__(1, tb.exact_representation(tabs, 1, d4, cap=cap1)), reps=2)
-    q = torch.linspace(-R2, R2, 4096, dtype=torch.float64, device=dev)
-    ms_e = _time_cuda(lambda: tb.ect_exact_eval(reps[0], q))
-    ms_r = _time_cuda(lambda: tb.radon_exact_eval(reps[0], reps[1], q))
-    rows["exact_2d"] = {
-        "workload": f"same {n_img} x 2048^2 tables; exact representations at 4 hybrid directions per image "
-                    "(sort of the FP64 dot products, ties merged), evaluated at 4096 thresholds",
-        "ect_rep_ms": ms0, "ect_rep_entries_per_s": ent0 / (ms0 / 1e3),
-        "radon_rep_ms": ms1, "radon_rep_entries_per_s": ent1 / (ms1 / 1e3),
-        "ect_eval_ms": ms_e, "radon_eval_ms": ms_r,
-        "evals_per_s": n_img * 4 * 4096 / (ms_e / 1e3),
-    }
-    del reps
+    if _want("sine_2d"):
+        # kappa = sin (the kernel of the paper's experiments)
+        o_sine = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
+        ms = _time_cuda(lambda: tb.hybrid_transform(tabs, "sine", dirs_ht, "fp32c", out=o_sine), reps=1)
+        rows["sine_2d"] = {"workload": "same tables; 4096 dirs, kappa = sin (kbar = -cos), FP32C",
+                           "ms": ms, "terms_per_s": terms / (ms / 1e3)}
+        del o_sine
 
-    # f2: top-dimensional construction of the same images (tables on the 2049^2 pixel
-    # corners): corner-image pre-pass + extraction, then the ECT at the 1024 x 512 grid
-    ttop = tb.tables_create(batch.shapes, batch.offsets, construction="top")
-    ms_top = _time_cuda(lambda: ttop.build(batch.pixels))
-    ttop.sync()
-    ntop = _sizes(ttop, n_img, 4)
-    ent_top = int(ntop[0].sum() + ntop[1][:, :2].sum())
-    out_top = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
-    ms_top_ect = _time_cuda(lambda: tb.ect(ttop, dirs_ect, -R2, R2, T_ECT, out=out_top))
-    rows["top_2d"] = {
-        "workload": f"same {n_img} x 2048^2 images, top-dimensional construction (tables on 2049^2 corners); "
-                    "extraction, then ECT at 1024 dirs x 512 thresholds",
-        "extract_ms": ms_top, "extract_gbs": (batch.pixels.numel() + 6 * ent_top) / (ms_top / 1e3) / 1e9,
-        "ect_ms": ms_top_ect, "ect_dirs_per_s": n_img * D_ECT / (ms_top_ect / 1e3),
-    }
-    ttop.free()
-    del out_top
+    if _want("table_2d"):
+        # a tabulated kernel, kbar given by K samples (piecewise linear, constant ends);
+        # here K = 1024 samples of sin(2 s) + 0.3 s^2 on [-R, R]
+        tab_rows = {}
+        for K in (64, 1024):
+            sk = -R2 + 2 * R2 / (K - 1) * np.arange(K)
+            kt = tb.KernelTable(np.sin(2.0 * sk) + 0.3 * sk * sk, -R2, R2)
+            o_tab = torch.empty((n_img, D_HT), dtype=torch.float64, device=dev)
+            ms = _time_cuda(lambda: tb.hybrid_transform(tabs, kt, dirs_ht, "fp32c", out=o_tab), reps=1)
+            tab_rows[f"K{K}_ms"] = ms
+            tab_rows[f"K{K}_terms_per_s"] = terms / (ms / 1e3)
+            del o_tab
+            kt.free()
+        rows["table_2d"] = {"workload": "same tables; 4096 dirs, kbar tabulated by K samples on [-R, R], FP32C",
+                            **tab_rows}
+
+    if _want("exact_2d"):
+        # exact representations (T, E) and (T', E') at 4 directions per image, and their
+        # evaluation at 4096 arbitrary thresholds
+        tabs.sync()                                   # sizes on the host (the step rebuilt the tables)
+        d4 = dirs_ht[:4].contiguous()
+        o4 = _orthants(dirs_ht_h[:4])
+        ent0 = int(sum(nl[:, o].sum() for o in o4))
+        ent1 = int(sum(nd[:, o if o < 2 else o ^ 3].sum() for o in o4))
+        cap0 = int(nl.max())
+        cap1 = int(nd.max())
+        reps = {}
+        ms0 = _time_cuda(lambda: reps.__setitem__(0, tb.exact_representation(tabs, 0, d4, cap=cap0)), reps=2)
+        ms1 = _time_cuda(lambda: reps.__setitem__(1, tb.exact_representation(tabs, 1, d4, cap=cap1)), reps=2)
+        q = torch.linspace(-R2, R2, 4096, dtype=torch.float64, device=dev)
+        ms_e = _time_cuda(lambda: tb.ect_exact_eval(reps[0], q))
+        ms_r = _time_cuda(lambda: tb.radon_exact_eval(reps[0], reps[1], q))
+        rows["exact_2d"] = {
+            "workload": f"same {n_img} x 2048^2 tables; exact representations at 4 hybrid directions per image "
+                        "(sort of the FP64 dot products, ties merged), evaluated at 4096 thresholds",
+            "ect_rep_ms": ms0, "ect_rep_entries_per_s": ent0 / (ms0 / 1e3),
+            "radon_rep_ms": ms1, "radon_rep_entries_per_s": ent1 / (ms1 / 1e3),
+            "ect_eval_ms": ms_e, "radon_eval_ms": ms_r,
+            "evals_per_s": n_img * 4 * 4096 / (ms_e / 1e3),
+        }
+        del reps
+
+    if _want("top_2d"):
+        # top-dimensional construction of the same images (tables on the 2049^2 pixel
+        # corners): corner-image pre-pass + extraction, then the ECT at the 1024 x 512 grid
+        ttop = tb.tables_create(batch.shapes, batch.offsets, construction="top")
+        ms_top = _time_cuda(lambda: ttop.build(batch.pixels))
+        ttop.sync()
+        ntop = _sizes(ttop, n_img, 4)
+        ent_top = int(ntop[0].sum() + ntop[1][:, :2].sum())
+        out_top = torch.empty((n_img, D_ECT, T_ECT), dtype=torch.int32, device=dev)
+        ms_top_ect = _time_cuda(lambda: tb.ect(ttop, dirs_ect, -R2, R2, T_ECT, out=out_top))
+        rows["top_2d"] = {
+            "workload": f"same {n_img} x 2048^2 images, top-dimensional construction (tables on 2049^2 corners); "
+                        "extraction, then ECT at 1024 dirs x 512 thresholds",
+            "extract_ms": ms_top, "extract_gbs": (batch.pixels.numel() + 6 * ent_top) / (ms_top / 1e3) / 1e9,
+            "ect_ms": ms_top_ect, "ect_dirs_per_s": n_img * D_ECT / (ms_top_ect / 1e3),
+        }
+        ttop.free()
+        del out_top
     return rows
 
 
 def ragged_workload():
-    """BASELINE configuration 4: 10,000 grey images, sides log-uniform in [28, 512] (non-square),
+    """The ragged batch: 10,000 grey images, sides log-uniform in [28, 512] (non-square),
     uniform noise blurred by sigma = 2 px; ECT directions (64 on the circle) and Laplace
     directions (256 unit vectors, uniform angle) shared by every image."""
     from paper_2405_02256_gb300 import synth
@@ -489,94 +507,97 @@ def ragged_pipeline(tb, batch, ect_h, ht_h, dev):
 
 
 def extra_workloads(dev):
-    """BASELINE configurations 3-5: 3-D volumes, ragged batch under a CUDA graph, gradients."""
+    """The ragged batch under a CUDA graph, 256^3 binary volumes, gradients on a 128^3 volume."""
     import torch
 
     from paper_2405_02256_gb300 import binding as tb
     from paper_2405_02256_gb300 import synth
     rows = {}
 
-    # configuration 4: 10,000 ragged grey images, one CUDA graph per step (tuned tiles)
-    t0 = time.time()
-    imgs, ect_h, ht_h = ragged_workload()
-    gen_s = time.time() - t0
-    batch = tb.pack_images(imgs, device=dev)
-    R2 = synth.image_radius(2)
-    pipe = ragged_pipeline(tb, batch, ect_h, ht_h, dev)
-    ms = _time_cuda(lambda: pipe.run(), reps=5)
-    # the three parts of the step, each launched on its own (outside the graph)
-    ect_d = torch.from_numpy(ect_h).to(dev)
-    ht_d = torch.from_numpy(ht_h).to(dev)
-    ect_o = torch.empty((len(imgs), 64, 64), dtype=torch.int32, device=dev)
-    ht_o = torch.empty((len(imgs), 256), dtype=torch.float64, device=dev)
-    ms_parts = {"extract_ms": _time_cuda(lambda: pipe.tables.build(pipe.pixels)),
-                "ect_ms": _time_cuda(lambda: tb.ect(pipe.tables, ect_d, -R2, R2, 64, out=ect_o)),
-                "laplace_ms": _time_cuda(lambda: tb.hybrid_transform(pipe.tables, "laplace", ht_d, "fp32c",
-                                                                     out=ht_o))}
-    pipe.tables.sync()
-    nl, nd = _sizes(pipe.tables, len(imgs), 4)
-    terms = int((nd * np.bincount(_orthants(ht_h), minlength=4)[None, :]).sum())
-    px = int(batch.pixels.numel())
-    rows["ragged_graph_2d"] = {
-        "workload": "10,000 grey images, sides log-uniform in [28, 512], blurred noise sigma 2; ECT 64 x 64 and "
-                    "Laplace at 256 unit dirs per image; extraction + ECT + Laplace replayed as one CUDA graph",
-        "ms_per_step": ms, "images_per_s": len(imgs) / (ms / 1e3), "pixels": px,
-        "ect_dirs_per_s": len(imgs) * 64 / (ms / 1e3), "laplace_terms_per_s_whole_step": terms / (ms / 1e3),
-        "laplace_terms_per_s": terms / (ms_parts["laplace_ms"] / 1e3),
-        "ect_updates_per_s": int((nl * np.bincount(_orthants(ect_h), minlength=4)[None, :]).sum())
-                             / (ms_parts["ect_ms"] / 1e3),
-        "tuned_tiles": pipe.tuned, "parts": ms_parts, "input_gen_s": gen_s}
-    pipe.tables.free()
-    del pipe, batch, imgs
+    if _want("ragged_graph_2d"):
+        # 10,000 ragged grey images, one CUDA graph per step (tuned tiles)
+        t0 = time.time()
+        imgs, ect_h, ht_h = ragged_workload()
+        gen_s = time.time() - t0
+        batch = tb.pack_images(imgs, device=dev)
+        R2 = synth.image_radius(2)
+        pipe = ragged_pipeline(tb, batch, ect_h, ht_h, dev)
+        ms = _time_cuda(lambda: pipe.run(), reps=5)
+        # the three parts of the step, each launched on its own (outside the graph)
+        ect_d = torch.from_numpy(ect_h).to(dev)
+        ht_d = torch.from_numpy(ht_h).to(dev)
+        ect_o = torch.empty((len(imgs), 64, 64), dtype=torch.int32, device=dev)
+        ht_o = torch.empty((len(imgs), 256), dtype=torch.float64, device=dev)
+        ms_parts = {"extract_ms": _time_cuda(lambda: pipe.tables.build(pipe.pixels)),
+                    "ect_ms": _time_cuda(lambda: tb.ect(pipe.tables, ect_d, -R2, R2, 64, out=ect_o)),
+                    "laplace_ms": _time_cuda(lambda: tb.hybrid_transform(pipe.tables, "laplace", ht_d, "fp32c",
+                                                                         out=ht_o))}
+        pipe.tables.sync()
+        nl, nd = _sizes(pipe.tables, len(imgs), 4)
+        terms = int((nd * np.bincount(_orthants(ht_h), minlength=4)[None, :]).sum())
+        px = int(batch.pixels.numel())
+        rows["ragged_graph_2d"] = {
+            "workload": "10,000 grey images, sides log-uniform in [28, 512], blurred noise sigma 2; ECT 64 x 64 and "
+                        "Laplace at 256 unit dirs per image; extraction + ECT + Laplace replayed as one CUDA graph",
+            "ms_per_step": ms, "images_per_s": len(imgs) / (ms / 1e3), "pixels": px,
+            "ect_dirs_per_s": len(imgs) * 64 / (ms / 1e3), "laplace_terms_per_s_whole_step": terms / (ms / 1e3),
+            "laplace_terms_per_s": terms / (ms_parts["laplace_ms"] / 1e3),
+            "ect_updates_per_s": int((nl * np.bincount(_orthants(ect_h), minlength=4)[None, :]).sum())
+                                 / (ms_parts["ect_ms"] / 1e3),
+            "tuned_tiles": pipe.tuned, "parts": ms_parts, "input_gen_s": gen_s}
+        pipe.tables.free()
+        del pipe, batch, imgs
 
-    # configuration 3: 4 binary volumes 256^3, ECT / Radon at 2048 Fibonacci dirs x 256, Fourier at 8192
-    vols = [synth.grf((256, 256, 256), 8.0, seed=300 + b, binary=True) for b in range(4)]
-    batch = tb.pack_images(vols, device=dev)
-    R3 = synth.image_radius(3)
-    fib = synth.fibonacci_dirs(2048)
-    four = synth.scale_norms(synth.fibonacci_dirs(8192), 3, 0.05, 2.0)
-    tabs = tb.tables_create(batch.shapes, batch.offsets)
-    ms_ext = _time_cuda(lambda: tabs.build(batch.pixels))
-    tabs.sync()
-    nl, nd = _sizes(tabs, 4, 8)
-    ent = int(nl.sum() + nd[:, :4].sum())
-    d_f = torch.from_numpy(fib).to(dev)
-    d_4 = torch.from_numpy(four).to(dev)
-    out = torch.empty((4, 2048, 256), dtype=torch.int32, device=dev)
-    ms_ect = _time_cuda(lambda: tb.ect(tabs, d_f, -R3, R3, 256, out=out))
-    ms_rad = _time_cuda(lambda: tb.radon(tabs, d_f, -R3, R3, 256, out=out))
-    o4 = torch.empty((4, 8192, 2), dtype=torch.float64, device=dev)
-    ms_f = _time_cuda(lambda: tb.hybrid_transform(tabs, "fourier", d_4, "fp32c", out=o4))
-    terms = int((nd * np.bincount(_orthants(four), minlength=8)[None, :]).sum())
-    rows["volumes_3d"] = {
-        "workload": "4 binary GRF volumes 256^3 (ell=8); ECT and Radon at 2048 Fibonacci dirs x 256; "
-                    "Fourier at 8192 dirs, |xi| uniform [0.05, 2]",
-        "extract_ms": ms_ext, "extract_gbs": (batch.pixels.numel() + 6 * ent) / (ms_ext / 1e3) / 1e9,
-        "ect_ms": ms_ect, "ect_dirs_per_s": 4 * 2048 / (ms_ect / 1e3),
-        "radon_ms": ms_rad, "radon_dirs_per_s": 4 * 2048 / (ms_rad / 1e3),
-        "fourier_ms": ms_f, "fourier_terms_per_s": terms / (ms_f / 1e3)}
-    tabs.free()
-    del batch, vols
+    if _want("volumes_3d"):
+        # 4 binary volumes 256^3, ECT / Radon at 2048 Fibonacci dirs x 256, Fourier at 8192
+        vols = [synth.grf((256, 256, 256), 8.0, seed=300 + b, binary=True) for b in range(4)]
+        batch = tb.pack_images(vols, device=dev)
+        R3 = synth.image_radius(3)
+        fib = synth.fibonacci_dirs(2048)
+        four = synth.scale_norms(synth.fibonacci_dirs(8192), 3, 0.05, 2.0)
+        tabs = tb.tables_create(batch.shapes, batch.offsets)
+        ms_ext = _time_cuda(lambda: tabs.build(batch.pixels))
+        tabs.sync()
+        nl, nd = _sizes(tabs, 4, 8)
+        ent = int(nl.sum() + nd[:, :4].sum())
+        d_f = torch.from_numpy(fib).to(dev)
+        d_4 = torch.from_numpy(four).to(dev)
+        out = torch.empty((4, 2048, 256), dtype=torch.int32, device=dev)
+        ms_ect = _time_cuda(lambda: tb.ect(tabs, d_f, -R3, R3, 256, out=out))
+        ms_rad = _time_cuda(lambda: tb.radon(tabs, d_f, -R3, R3, 256, out=out))
+        o4 = torch.empty((4, 8192, 2), dtype=torch.float64, device=dev)
+        ms_f = _time_cuda(lambda: tb.hybrid_transform(tabs, "fourier", d_4, "fp32c", out=o4))
+        terms = int((nd * np.bincount(_orthants(four), minlength=8)[None, :]).sum())
+        rows["volumes_3d"] = {
+            "workload": "4 binary GRF volumes 256^3 (ell=8); ECT and Radon at 2048 Fibonacci dirs x 256; "
+                        "Fourier at 8192 dirs, |xi| uniform [0.05, 2]",
+            "extract_ms": ms_ext, "extract_gbs": (batch.pixels.numel() + 6 * ent) / (ms_ext / 1e3) / 1e9,
+            "ect_ms": ms_ect, "ect_dirs_per_s": 4 * 2048 / (ms_ect / 1e3),
+            "radon_ms": ms_rad, "radon_dirs_per_s": 4 * 2048 / (ms_rad / 1e3),
+            "fourier_ms": ms_f, "fourier_terms_per_s": terms / (ms_f / 1e3)}
+        tabs.free()
+        del batch, vols
 
-    # configuration 5: one 128^3 grey volume, Laplace and Fourier forward + adjoint at 8192 dirs
-    vol = synth.grf((128, 128, 128), 6.0, seed=5)
-    batch = tb.pack_images([vol], device=dev)
-    tabs = tb.build_critical_tables(batch)
-    xi = synth.sphere_dirs(8192, 6, 0.1, 1.0)
-    d = torch.from_numpy(xi).to(dev)
-    nl, nd = _sizes(tabs, 1, 8)
-    terms = int((nd * np.bincount(_orthants(xi), minlength=8)[None, :]).sum())
-    res = {}
-    for k in ("laplace", "fourier"):
-        o = torch.empty((1, 8192, 2) if k == "fourier" else (1, 8192), dtype=torch.float64, device=dev)
-        ms_fw = _time_cuda(lambda: tb.hybrid_transform(tabs, k, d, "fp32c", out=o))
-        g = torch.empty_like(d)
-        gout = torch.ones_like(o)
-        ms_bw = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, d, gout, "fp32c", out=g))
-        res[k] = {"forward_ms": ms_fw, "adjoint_ms": ms_bw, "forward_terms_per_s": terms / (ms_fw / 1e3),
-                  "adjoint_terms_per_s": terms / (ms_bw / 1e3)}
-    rows["gradients_3d"] = {"workload": "128^3 grey GRF (ell=6); 8192 dirs, |xi| in [0.1, 1]", **res}
-    tabs.free()
+    if _want("gradients_3d"):
+        # one 128^3 grey volume, Laplace and Fourier forward + adjoint at 8192 dirs
+        vol = synth.grf((128, 128, 128), 6.0, seed=5)
+        batch = tb.pack_images([vol], device=dev)
+        tabs = tb.build_critical_tables(batch)
+        xi = synth.sphere_dirs(8192, 6, 0.1, 1.0)
+        d = torch.from_numpy(xi).to(dev)
+        nl, nd = _sizes(tabs, 1, 8)
+        terms = int((nd * np.bincount(_orthants(xi), minlength=8)[None, :]).sum())
+        res = {}
+        for k in ("laplace", "fourier"):
+            o = torch.empty((1, 8192, 2) if k == "fourier" else (1, 8192), dtype=torch.float64, device=dev)
+            ms_fw = _time_cuda(lambda: tb.hybrid_transform(tabs, k, d, "fp32c", out=o))
+            g = torch.empty_like(d)
+            gout = torch.ones_like(o)
+            ms_bw = _time_cuda(lambda: tb.hybrid_transform_grad(tabs, k, d, gout, "fp32c", out=g))
+            res[k] = {"forward_ms": ms_fw, "adjoint_ms": ms_bw, "forward_terms_per_s": terms / (ms_fw / 1e3),
+                      "adjoint_terms_per_s": terms / (ms_bw / 1e3)}
+        rows["gradients_3d"] = {"workload": "128^3 grey GRF (ell=6); 8192 dirs, |xi| in [0.1, 1]", **res}
+        tabs.free()
     return rows
 
 
@@ -698,7 +719,13 @@ def main():
     p.add_argument("--cpu-budget", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the other rows and configurations")
+    p.add_argument("--rows", default=None,
+                   help="comma-separated extra rows to run (radon_2d, adjoint_2d, sine_2d, table_2d, exact_2d, "
+                        "top_2d, ragged_graph_2d, volumes_3d, gradients_3d); default all")
     args = p.parse_args()
+    if args.rows:
+        global _ROWS
+        _ROWS = set(args.rows.split(","))
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -14,7 +14,7 @@
 //
 // Steps, per (image, direction) segment, all on the device:
 //   keys   : s_v exactly as the canonical FP64 dot product (one rounding per product and
-//            per sum, left to right), -0 turned into +0, mapped to an unsigned 64-bit key
+//            per sum, left to right), mapped (-0 with +0) to an unsigned 64-bit key
 //            whose order is the order of the doubles.  The products xi_k x_k(c) of one
 //            direction take m_0 + ... + m_{n-1} values; a block stages them in shared
 //            memory once per direction, so that an entry costs n - 1 FP64 additions and no
@@ -50,8 +50,10 @@ constexpr unsigned long long kRadixA = 1ull << 58;
 constexpr unsigned long long kRadixP = 2ull << 58;
 constexpr unsigned long long kRadixCount = (1ull << 58) - 1;
 
+// -0 and +0 map to one key (that of +0)
 __device__ __forceinline__ unsigned long long order_key(double s) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+    unsigned long long u = (unsigned long long)__double_as_longlong(s);
+    if (u == (1ull << 63)) u = 0ull;
     return (u >> 63) ? ~u : (u | (1ull << 63));
 }
 
@@ -166,7 +168,6 @@ __global__ void __launch_bounds__(kKeysThreads) k_exact_keys(ExactArgs a) {
                     const double pk = staged ? prod[off[k] + c[k]] : __dmul_rn(x[k], vertex_coord(c[k], mm[k]));
                     s = k == 0 ? pk : __dadd_rn(s, pk);
                 }
-                s = __dadd_rn(s, 0.0);              // -0 -> +0: one key per value
                 key = order_key(s);
                 K[i] = key;
                 V[i] = sg * (int)av[i];

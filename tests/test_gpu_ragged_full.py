@@ -1,4 +1,4 @@
-"""BASELINE configuration 4 at full size, in the launch configuration bench.py times:
+"""The 10,000-image ragged batch at full size, in the launch configuration bench.py times:
 10,000 ragged grey images (sides 28-512) in one CUDA graph with tuned tiles, ECT at 64
 directions x 64 thresholds and Laplace at 256 directions (FP32C).  Sampled images --
 the largest, the smallest and random ones -- are checked against the oracle: tables and

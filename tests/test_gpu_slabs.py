@@ -128,7 +128,7 @@ def test_slab_errors(tb):
 
 
 def test_slabs_256_cube(tb, sl):
-    """BASELINE configuration 3's volume size: one 256^3 binary GRF volume in 4 slabs;
+    """The 256^3 binary GRF volume of the volume workload in 4 slabs;
     ECT and Radon at 2048 Fibonacci directions x 256 thresholds bit-exact against the
     whole volume, Fourier at 8192 directions within 2e-6 of the whole volume's FP32C
     result relative to sum |Delta kbar| (the oracle's, on 96 sampled directions, within 1e-6)."""
