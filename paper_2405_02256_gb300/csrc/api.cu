@@ -83,6 +83,7 @@ struct topot_tables {
     long long* absum = nullptr;
     unsigned* err = nullptr;
     unsigned* ticket = nullptr;
+    int2* order = nullptr;            // [num_tiles] extraction order: (image, local tile)
     unsigned long long* status = nullptr;
     long long* vsum = nullptr;        // [B][S] sum of the values of each table (slabs)
     bool slab = false;                // tables of slabs of volumes (tables_create_slab)
@@ -366,6 +367,7 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         return o;
     };
     const size_t o_img = place(sizeof(ImgDesc) * B);
+    const size_t o_ord = place(sizeof(int2) * (size_t)tiles);
     const size_t o_cnt = place(sizeof(long long) * B * t->S);
     const size_t o_err = place(sizeof(unsigned));
     const size_t o_chi = place(sizeof(long long) * B);
@@ -388,6 +390,7 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
     t->chi = reinterpret_cast<long long*>(m + o_chi);
     t->absum = reinterpret_cast<long long*>(m + o_abs);
     t->ticket = reinterpret_cast<unsigned*>(m + o_tic);
+    t->order = reinterpret_cast<int2*>(m + o_ord);
     t->status = reinterpret_cast<unsigned long long*>(m + o_sta);
     t->vsum = reinterpret_cast<long long*>(m + o_vsum);
     t->slab = h_zrange != nullptr;
@@ -408,6 +411,24 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         }
     }
     e = cudaMemcpy(t->d_img, t->h_img.data(), sizeof(ImgDesc) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t->gen) {
+        // Extraction order: round robin over the images by local tile index.  The look-back
+        // of a tile waits only on earlier tiles of its own image; interleaving the images
+        // keeps few tiles of any one image in flight, so its prefix chain is short.
+        std::vector<int2> order;
+        order.reserve((size_t)tiles);
+        std::vector<long long> ntile(B);
+        long long most = 0;
+        for (int b = 0; b < B; ++b) {
+            const long long nb = (b + 1 < B ? t->h_img[b + 1].tile_begin : tiles) - t->h_img[b].tile_begin;
+            ntile[b] = nb;
+            most = std::max(most, nb);
+        }
+        for (long long lt = 0; lt < most; ++lt)
+            for (int b = 0; b < B; ++b)
+                if (lt < ntile[b]) order.push_back(make_int2(b, (int)lt));
+        e = cudaMemcpy(t->order, order.data(), sizeof(int2) * (size_t)tiles, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemset(t->seg_count, 0, o_chi - o_cnt);   // counts + error word
     if (e != cudaSuccess) {
         free_tables(t);
@@ -447,6 +468,7 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     a.pixels = d_pixels;
     a.num_tiles = t->num_tiles;
     a.ticket = t->ticket;
+    a.order = t->order;
     a.status = t->status;
     a.row_stride = t->row_stride;
     a.stage_rows = t->stage_rows;

@@ -214,15 +214,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_extract(ExtractArgs p) {
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
+        // ticket -> (image, local tile) -> global tile number, which indexes the look-back
         const unsigned ticket = atomicAdd(p.ticket, 1u);
-        // image owning this tile: last b with tile_begin <= ticket
-        int lo = 0, hi = T.B - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (T.img[mid].tile_begin <= (long long)ticket) lo = mid; else hi = mid - 1;
-        }
-        sh_int[0] = (int)ticket;
-        sh_int[1] = lo;
+        const int2 bl = p.order[ticket];
+        sh_int[0] = (int)(T.img[bl.x].tile_begin + bl.y);
+        sh_int[1] = bl.x;
     }
     if (tid < 1 + NO) sh_acc[tid] = 0;
     __syncthreads();

@@ -529,16 +529,15 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
+        // ticket -> (image, local tile) -> global tile number, which indexes the look-back
         const unsigned ticket = atomicAdd(p.ticket, 1u);
-        int lo = 0, hi = T.B - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&T.img[mid].tile_begin) <= (long long)ticket) lo = mid; else hi = mid - 1;
-        }
-        sh_int[0] = (int)ticket;
+        const int2 bl = __ldg(&p.order[ticket]);
+        const int lo = bl.x;
+        const long long gt = __ldg(&T.img[lo].tile_begin) + bl.y;
+        sh_int[0] = (int)gt;
         sh_int[1] = lo;
         // the tile's bulk copies go out before the block synchronises
-        const TileGeo g0 = tile_geometry<NDIM, TOP>(p, lo, ticket);
+        const TileGeo g0 = tile_geometry<NDIM, TOP>(p, lo, gt);
         if (TOP) issue_top_copies<NDIM>(g0, __ldg(&T.img[lo].top_pitch), stage, bar);
         else issue_stage_copies<NDIM>(g0, stage, bar);
     }

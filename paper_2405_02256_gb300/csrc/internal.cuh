@@ -106,7 +106,8 @@ struct ExtractArgs {
     const void* pixels;
     long long num_tiles;
     unsigned* ticket;                 // zeroed before launch
-    unsigned long long* status;       // [num_tiles * S] look-back words, zeroed before launch
+    const int2* order;                // [num_tiles] (image, local tile) taken by ticket t
+    unsigned long long* status;       // [num_tiles * S] look-back words (global tile numbers)
     int row_stride;                   // staged row stride (elements, 16-byte multiple)
     int stage_rows;                   // staged rows per plane (max R + 2)
     int stage_bytes;                  // 8-bit kernel: staged bytes per tile (max over images)
