@@ -39,19 +39,19 @@ namespace {
 
 template <int NDIM> struct U8Cfg;
 template <> struct U8Cfg<2> {
-    static constexpr int B = 512;       // threads per block
+    static constexpr int B = 256;       // threads per block
     static constexpr int STRIP = 8;     // vertices per thread
-    static constexpr int MINB = 2;      // resident blocks per SM (registers <= 64)
+    static constexpr int MINB = 4;      // resident blocks per SM (registers <= 64)
 };
 template <> struct U8Cfg<3> {
-    static constexpr int B = 512;
+    static constexpr int B = 512;       // 3-D: larger tiles (2048 voxels) halve the per-tile cost
     static constexpr int STRIP = 4;
     static constexpr int MINB = 2;      // registers <= 64
 };
 
 constexpr int kPadB = 16;               // staged row interior starts 16 bytes in
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kHdr = 2048;              // shared-memory header bytes
+constexpr int kHdrPerWarp = 128;       // shared-memory header bytes per warp
 
 template <int NDIM> struct U8Layout {
     static constexpr int B = U8Cfg<NDIM>::B;
@@ -69,9 +69,9 @@ template <int NDIM> struct U8Layout {
     static constexpr int OFF_WEX = OFF_WSUM + NW * 32;        // [NW][8] words
     static constexpr int OFF_TOT = OFF_WEX + NW * 32;         // [8] words
     static constexpr int OFF_PREF = OFF_TOT + 32;             // [SEG] long long
-    static constexpr int OFF_OUT = kHdr;                       // [SEG * CAP] words
+    static constexpr int OFF_OUT = NW * kHdrPerWarp;          // [SEG * CAP] words
     static constexpr int OFF_STAGE = OFF_OUT + 4 * SEG * CAP;
-    static_assert(OFF_PREF + 8 * SEG <= kHdr, "shared-memory header too small");
+    static_assert(OFF_PREF + 8 * SEG <= NW * kHdrPerWarp, "shared-memory header too small");
     static_assert(CAP <= 65536, "tile-local vertex index must fit 16 bits");
 };
 
