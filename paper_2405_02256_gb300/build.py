@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtopot.so")
-SOURCES = ["extract.cu", "extract_u8.cu", "plan.cu", "ect.cu", "ht.cu", "exact.cu", "slab.cu", "generic.cu",
+SOURCES = ["extract.cu", "extract_u8.cu", "binary3.cu", "plan.cu", "ect.cu", "ht.cu", "exact.cu", "slab.cu", "generic.cu",
            "selftest.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

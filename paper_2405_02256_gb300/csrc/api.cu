@@ -33,6 +33,9 @@ cudaError_t launch_extract_u8(int n, bool top, const ExtractArgs& a, cudaStream_
 cudaError_t launch_selftest_wait(int which, unsigned long long limit_ns, unsigned long long* flag, unsigned* err,
                                  cudaStream_t st);
 int extract_u8_threads(int n);
+int bin_unit_warps();
+int bin_chunk();
+cudaError_t launch_bin3(const BinArgs& a, int B, int pack_blocks_per_image, cudaStream_t st);
 int extract_u8_strip(int n);
 size_t extract_u8_smem_bytes(int n, int stage_bytes);
 size_t hist_smem_bytes(int td, int T);
@@ -86,6 +89,11 @@ struct topot_tables {
     int2* order = nullptr;            // [num_tiles] extraction order: (image, local tile)
     unsigned long long* status = nullptr;
     long long* vsum = nullptr;        // [B][S] sum of the values of each table (slabs)
+    // 3-D 8-bit whole volumes: the binary path (binary3.cu) for volumes of 0 / 1 voxels
+    bool bin3 = false;
+    void* bbuf = nullptr;
+    BinArgs bin{};
+    int bin_pack_blocks = 1;
     bool slab = false;                // tables of slabs of volumes (tables_create_slab)
     size_t clear_bytes = 0;           // bytes from `chi` to the end of `vsum` zeroed per build
     int* arena_idx = nullptr;
@@ -411,6 +419,74 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
         }
     }
     e = cudaMemcpy(t->d_img, t->h_img.data(), sizeof(ImgDesc) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && t->u8 && n == 3 && !top && !h_zrange && B <= 65535) {
+        // binary path: packed bits (zero border), per-unit counts and offsets, block and
+        // chunk lists
+        const long long U = 32, UW = bin_unit_warps(), C = bin_chunk();
+        std::vector<BinImg> bi(B);
+        std::vector<int2> blk, chk;
+        long long pk = 0, ub = 0, most = 1;
+        for (int b = 0; b < B; ++b) {
+            const ImgDesc& I = t->h_img[b];
+            BinImg& Q = bi[b];
+            Q.pix_off = h_offsets[b];
+            Q.m0 = I.m[0];
+            Q.m1 = I.m[1];
+            Q.m2 = I.m[2];
+            Q.wpr = (I.m[0] + 31) / 32;
+            const long long nw = (long long)Q.m2 * Q.m1 * Q.wpr;
+            Q.nunits = (int)((nw + U - 1) / U);
+            Q.pk_off = pk;
+            Q.unit_begin = ub;
+            Q.seg_base = I.seg_base;
+            Q.N = I.N;
+            Q.div_wpr = make_fastdiv((uint32_t)Q.wpr);
+            Q.div_m1 = make_fastdiv((uint32_t)Q.m1);
+            pk += ((long long)(Q.m2 + 2) * (Q.m1 + 2) * (Q.wpr + 2) + 3) & ~3ll;
+            ub += Q.nunits;
+            most = std::max(most, nw);
+            for (long long lu = 0; lu < Q.nunits; lu += UW) blk.push_back(make_int2(b, (int)lu));
+            for (long long j = 0; j * C < Q.nunits; ++j) chk.push_back(make_int2(b, (int)j));
+        }
+        size_t bo = 0;
+        auto bplace = [&](size_t bytes) {
+            bo = align_up(bo, 256);
+            const size_t o = bo;
+            bo += bytes;
+            return o;
+        };
+        const size_t o_bi = bplace(sizeof(BinImg) * B);
+        const size_t o_pk = bplace(sizeof(uint32_t) * (size_t)pk);
+        const size_t o_nb = bplace(sizeof(unsigned) * (B + 1));
+        const size_t o_uc = bplace(sizeof(uint32_t) * 6 * (size_t)ub);
+        const size_t o_uo = bplace(sizeof(int) * 12 * (size_t)ub);
+        const size_t o_cs = bplace(sizeof(int) * 12 * chk.size());
+        const size_t o_bl = bplace(sizeof(int2) * blk.size());
+        const size_t o_ch = bplace(sizeof(int2) * chk.size());
+        e = cudaMalloc(&t->bbuf, bo);
+        if (e == cudaSuccess) {
+            char* q = reinterpret_cast<char*>(t->bbuf);
+            BinArgs& a = t->bin;
+            a.img = reinterpret_cast<BinImg*>(q + o_bi);
+            a.packed = reinterpret_cast<uint32_t*>(q + o_pk);
+            a.nonbin = reinterpret_cast<unsigned*>(q + o_nb);
+            a.ucount = reinterpret_cast<uint32_t*>(q + o_uc);
+            a.uoff = reinterpret_cast<int*>(q + o_uo);
+            a.csum = reinterpret_cast<int*>(q + o_cs);
+            a.blocks = reinterpret_cast<int2*>(q + o_bl);
+            a.nblocks = (int)blk.size();
+            a.chunks = reinterpret_cast<int2*>(q + o_ch);
+            a.nchunks = (int)chk.size();
+            e = cudaMemcpy(q + o_bi, bi.data(), sizeof(BinImg) * B, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemset(q + o_pk, 0, sizeof(uint32_t) * (size_t)pk);   // borders stay 0
+            if (e == cudaSuccess)
+                e = cudaMemcpy(q + o_bl, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(q + o_ch, chk.data(), sizeof(int2) * chk.size(), cudaMemcpyHostToDevice);
+            t->bin3 = true;
+            t->bin_pack_blocks = (int)std::min<long long>((most + 255) / 256, std::max(1, 4 * t->sm_count / B));
+        }
+    }
     if (e == cudaSuccess && !t->gen) {
         // Extraction order: round robin over the images by local tile index.  The look-back
         // of a tile waits only on earlier tiles of its own image; interleaving the images
@@ -470,6 +546,7 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
     a.ticket = t->ticket;
     a.order = t->order;
     a.status = t->status;
+    a.nonbin = nullptr;
     a.row_stride = t->row_stride;
     a.stage_rows = t->stage_rows;
     a.stage_bytes = t->stage_bytes;
@@ -489,6 +566,15 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
         a.pixels = t->d_corner;
         TOPOT_CUDA(launch_extract(t->n, t->dtype, true, a, st));
     } else if (t->u8) {
+        if (t->bin3) {
+            // binary volumes first; the general kernel skips them
+            BinArgs b = t->bin;
+            b.t = t->dev();
+            b.pixels = d_pixels;
+            TOPOT_CUDA(cudaMemsetAsync(b.nonbin, 0, sizeof(unsigned) * (t->B + 1), st));
+            TOPOT_CUDA(launch_bin3(b, t->B, t->bin_pack_blocks, st));
+            a.nonbin = b.nonbin;
+        }
         TOPOT_CUDA(launch_extract_u8(t->n, false, a, st));
     } else {
         TOPOT_CUDA(launch_extract(t->n, t->dtype, false, a, st));
@@ -604,6 +690,7 @@ void free_tables(topot_tables* t) {
     for (int f = 0; f < kWsFamilies; ++f)
         if (t->ws[f]) cudaFree(t->ws[f]);
     if (t->top_buf) cudaFree(t->top_buf);
+    if (t->bbuf) cudaFree(t->bbuf);
     if (t->arena_val) cudaFree(t->arena_val);
     if (t->arena_idx) cudaFree(t->arena_idx);
     if (t->meta) cudaFree(t->meta);

@@ -525,6 +525,8 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const TablesDev& T = p.t;
+    // every volume binary: the binary kernels built all tables (grid-uniform)
+    if (p.nonbin && __ldg(&p.nonbin[T.B]) == 0u) return;
 
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -536,15 +538,20 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
         const long long gt = __ldg(&T.img[lo].tile_begin) + bl.y;
         sh_int[0] = (int)gt;
         sh_int[1] = lo;
-        // the tile's bulk copies go out before the block synchronises
-        const TileGeo g0 = tile_geometry<NDIM, TOP>(p, lo, gt);
-        if (TOP) issue_top_copies<NDIM>(g0, __ldg(&T.img[lo].top_pitch), stage, bar);
-        else issue_stage_copies<NDIM>(g0, stage, bar);
+        if (p.nonbin && __ldg(&p.nonbin[lo]) == 0u) {
+            sh_int[1] = -1;   // a binary volume: the binary kernels build its tables
+        } else {
+            // the tile's bulk copies go out before the block synchronises
+            const TileGeo g0 = tile_geometry<NDIM, TOP>(p, lo, gt);
+            if (TOP) issue_top_copies<NDIM>(g0, __ldg(&T.img[lo].top_pitch), stage, bar);
+            else issue_stage_copies<NDIM>(g0, stage, bar);
+        }
     }
     __syncthreads();
 
     const long long ticket = (unsigned)sh_int[0];
     const int b = sh_int[1];
+    if (b < 0) return;   // block-uniform; no copy was issued
     const ImgDesc* Ip = T.img + b;
     const TileGeo G = tile_geometry<NDIM, TOP>(p, b, ticket);
     const int m0 = G.m0, m1 = G.m1, m2 = G.m2, R = G.R, spr = G.spr, RS = G.RS, tpp = G.tpp;

@@ -111,6 +111,39 @@ struct ExtractArgs {
     int row_stride;                   // staged row stride (elements, 16-byte multiple)
     int stage_rows;                   // staged rows per plane (max R + 2)
     int stage_bytes;                  // 8-bit kernel: staged bytes per tile (max over images)
+    const unsigned* nonbin;           // 3-D 8-bit: [B + 1] from the binary path (null without it)
+};
+
+// Binary 8-bit volumes (all voxels 0 or 1): per volume, its packed bits and units.
+// The packed bits keep a zero border: (m_2 + 2) planes of (m_1 + 2) rows of (wpr + 2)
+// words, voxel word (z, y, xw) at pk_off + ((z + 1)(m_1 + 2) + y + 1)(wpr + 2) + xw + 1, so
+// every neighbour word is a fixed offset away and needs no bounds check.
+struct BinImg {
+    long long pix_off;      // element offset of the voxels in the pixel buffer
+    long long pk_off;       // word offset of the packed bits
+    long long unit_begin;   // first unit (32 consecutive voxel words) in the global numbering
+    long long seg_base;     // arena slot of segment 0 (segments are N apart)
+    long long N;            // vertices
+    int m0, m1, m2;
+    int wpr;                // voxel words per row: ceil(m_0 / 32)
+    int nunits;             // ceil(m_2 m_1 wpr / 32)
+    FastDiv div_wpr;        // division by wpr
+    FastDiv div_m1;         // division by m_1
+};
+
+struct BinArgs {
+    TablesDev t;
+    const BinImg* img;      // [B]
+    const void* pixels;
+    uint32_t* packed;
+    unsigned* nonbin;       // [B + 1] volume b has a voxel above 1; [B]: some volume has (zeroed per build)
+    uint32_t* ucount;       // [units][6] per-unit counts, two 16-bit fields per word
+    int* uoff;              // [units][12] per-unit offsets within each segment
+    int* csum;              // [nchunks][12]
+    const int2* blocks;     // [nblocks] (volume, first unit) of each block of the two passes
+    int nblocks;
+    const int2* chunks;     // [nchunks] (volume, chunk of the volume), volume-major
+    int nchunks;
 };
 
 // Top-dimensional construction: per image, where its pixels and its corner image live.
