@@ -378,6 +378,15 @@ def _sizes(tabs, n_img, NO):
 _ROWS = None   # names of the extra rows to run (None: all)
 
 
+def _hbm_gbs() -> float:
+    """Measured HBM copy bandwidth (GB/s) of this machine's GPUs, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    except OSError:
+        return 6800.0
+
+
 def _want(name: str) -> bool:
     return _ROWS is None or name in _ROWS
 
@@ -476,6 +485,7 @@ def extra_rows(tabs, batch, dirs_ect, dirs_ect_h, dirs_ht, dirs_ht_h, nl, nd, n_
             "workload": f"same {n_img} x 2048^2 images, top-dimensional construction (tables on 2049^2 corners); "
                         "extraction, then ECT at 1024 dirs x 512 thresholds",
             "extract_ms": ms_top, "extract_gbs": (batch.pixels.numel() + 6 * ent_top) / (ms_top / 1e3) / 1e9,
+            "extract_hbm_frac": (batch.pixels.numel() + 6 * ent_top) / (ms_top / 1e3) / 1e9 / _hbm_gbs(),
             "ect_ms": ms_top_ect, "ect_dirs_per_s": n_img * D_ECT / (ms_top_ect / 1e3),
         }
         ttop.free()
@@ -572,6 +582,8 @@ def extra_workloads(dev):
             "workload": "4 binary GRF volumes 256^3 (ell=8); ECT and Radon at 2048 Fibonacci dirs x 256; "
                         "Fourier at 8192 dirs, |xi| uniform [0.05, 2]",
             "extract_ms": ms_ext, "extract_gbs": (batch.pixels.numel() + 6 * ent) / (ms_ext / 1e3) / 1e9,
+            "extract_hbm_frac": (batch.pixels.numel() + 6 * ent) / (ms_ext / 1e3) / 1e9 / _hbm_gbs(),
+            "extract_path": "binary volumes: bit-sliced pack, count, scan and write kernels",
             "ect_ms": ms_ect, "ect_dirs_per_s": 4 * 2048 / (ms_ect / 1e3),
             "radon_ms": ms_rad, "radon_dirs_per_s": 4 * 2048 / (ms_rad / 1e3),
             "fourier_ms": ms_f, "fourier_terms_per_s": terms / (ms_f / 1e3)}
