@@ -35,7 +35,8 @@ cudaError_t launch_selftest_wait(int which, unsigned long long limit_ns, unsigne
 int extract_u8_threads(int n);
 int bin_unit_warps();
 int bin_chunk();
-cudaError_t launch_bin3(const BinArgs& a, int B, int pack_blocks_per_image, cudaStream_t st);
+cudaError_t launch_bin_pack(const BinArgs& a, int B, int pack_blocks_per_image, cudaStream_t st);
+cudaError_t launch_bin_tables(const BinArgs& a, cudaStream_t st);
 int extract_u8_strip(int n);
 size_t extract_u8_smem_bytes(int n, int stage_bytes);
 size_t hist_smem_bytes(int td, int T);
@@ -94,6 +95,8 @@ struct topot_tables {
     void* bbuf = nullptr;
     BinArgs bin{};
     int bin_pack_blocks = 1;
+    cudaStream_t side = nullptr;      // the general kernel runs here beside the binary kernels
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool slab = false;                // tables of slabs of volumes (tables_create_slab)
     size_t clear_bytes = 0;           // bytes from `chi` to the end of `vsum` zeroed per build
     int* arena_idx = nullptr;
@@ -483,6 +486,9 @@ static topot_status create_impl(topot_dtype dtype, int n, const int64_t* h_shape
                 e = cudaMemcpy(q + o_bl, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice);
             if (e == cudaSuccess)
                 e = cudaMemcpy(q + o_ch, chk.data(), sizeof(int2) * chk.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming);
             t->bin3 = true;
             t->bin_pack_blocks = (int)std::min<long long>((most + 255) / 256, std::max(1, 4 * t->sm_count / B));
         }
@@ -567,15 +573,24 @@ topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream) {
         TOPOT_CUDA(launch_extract(t->n, t->dtype, true, a, st));
     } else if (t->u8) {
         if (t->bin3) {
-            // binary volumes first; the general kernel skips them
+            // The pack flags the volumes that are not binary.  Then the general kernel (which
+            // skips binary volumes) runs on the side stream while the binary kernels run on
+            // `st`; the two touch disjoint tables, and `st` waits for both.
             BinArgs b = t->bin;
             b.t = t->dev();
             b.pixels = d_pixels;
             TOPOT_CUDA(cudaMemsetAsync(b.nonbin, 0, sizeof(unsigned) * (t->B + 1), st));
-            TOPOT_CUDA(launch_bin3(b, t->B, t->bin_pack_blocks, st));
+            TOPOT_CUDA(launch_bin_pack(b, t->B, t->bin_pack_blocks, st));
             a.nonbin = b.nonbin;
+            TOPOT_CUDA(cudaEventRecord(t->ev_fork, st));
+            TOPOT_CUDA(cudaStreamWaitEvent(t->side, t->ev_fork, 0));
+            TOPOT_CUDA(launch_extract_u8(t->n, false, a, t->side));
+            TOPOT_CUDA(cudaEventRecord(t->ev_join, t->side));
+            TOPOT_CUDA(launch_bin_tables(b, st));
+            TOPOT_CUDA(cudaStreamWaitEvent(st, t->ev_join, 0));
+        } else {
+            TOPOT_CUDA(launch_extract_u8(t->n, false, a, st));
         }
-        TOPOT_CUDA(launch_extract_u8(t->n, false, a, st));
     } else {
         TOPOT_CUDA(launch_extract(t->n, t->dtype, false, a, st));
     }
@@ -691,6 +706,9 @@ void free_tables(topot_tables* t) {
         if (t->ws[f]) cudaFree(t->ws[f]);
     if (t->top_buf) cudaFree(t->top_buf);
     if (t->bbuf) cudaFree(t->bbuf);
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    if (t->ev_join) cudaEventDestroy(t->ev_join);
+    if (t->side) cudaStreamDestroy(t->side);
     if (t->arena_val) cudaFree(t->arena_val);
     if (t->arena_idx) cudaFree(t->arena_idx);
     if (t->meta) cudaFree(t->meta);

@@ -327,10 +327,13 @@ __global__ void __launch_bounds__(kBChunk) k_bin_scan(BinArgs a) {
 int bin_unit_warps() { return kUnitWarps; }
 int bin_chunk() { return kBChunk; }
 
-cudaError_t launch_bin3(const BinArgs& a, int B, int pack_blocks_per_image, cudaStream_t st) {
+cudaError_t launch_bin_pack(const BinArgs& a, int B, int pack_blocks_per_image, cudaStream_t st) {
     k_bin_pack<<<dim3((unsigned)pack_blocks_per_image, (unsigned)B), 256, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_tables(const BinArgs& a, cudaStream_t st) {
+    cudaError_t e;
     k_bin_extract<false><<<(unsigned)a.nblocks, 32 * kUnitWarps, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_bin_chunk_sum<<<(unsigned)a.nchunks, kBChunk, 0, st>>>(a);

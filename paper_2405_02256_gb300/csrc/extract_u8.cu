@@ -826,77 +826,83 @@ __global__ void __launch_bounds__(U8Cfg<NDIM>::B, U8Cfg<NDIM>::MINB) k_extract_u
     __syncthreads();
 
     // ---- 6. write the tile's runs; chi and sum |Delta^-_o| from the lower tables -------------
-    // Each segment's run starts at an arbitrary arena position g0.  It is written in groups
-    // of four arena slots aligned to four (one 16-byte index store, one 8-byte value store);
-    // the partial groups at the two ends store entry by entry.  Group numbers continue
-    // across segments modulo the block size, so that every thread gets about the same
-    // number of groups.
-    int red[1 + kNO];
-#pragma unroll
-    for (int i = 0; i <= kNO; ++i) red[i] = 0;
+    // Each warp writes one segment: a lower table, or half of a Delta table (about twice as
+    // dense), so a thread sets up one run, not every segment's.  A run starts at an
+    // arbitrary arena position g0 and is written in groups of four arena slots aligned to
+    // four (one 16-byte index store, one 8-byte value store); the partial groups at the two
+    // ends store entry by entry.
+    static_assert(kNW == kNO + 2 * (kNO / 2), "one warp per lower table, two per Delta table");
     const FastDiv divp = TOP ? ldg_fastdiv(&Ip->div_pitch) : FastDiv{0u, 0u, 0u};
     const int top_p = TOP ? __ldg(&Ip->top_pitch) : 0;
-    {
-        uint32_t base = 0, cum = 0;
+    const int sw = warp < kNO ? warp : kNO + ((warp - kNO) >> 1);   // this warp's segment
+    const int part = warp < kNO ? 0 : ((warp - kNO) & 1);
+    const int nparts = warp < kNO ? 1 : 2;
+    uint32_t base = 0, nseg = 0;
 #pragma unroll
-        for (int s = 0; s < kSeg; ++s) {
-            const int n = (int)field16(tot, s);
-            const long long g0 = sh_pref[s];
-            const int ph = (int)(g0 & 3);
-            const int ngroups = (ph + n + 3) >> 2;
-            int* __restrict__ pi = T.arena_idx + (g0 - ph);
-            int16_t* __restrict__ pv = reinterpret_cast<int16_t*>(T.arena_val) + (g0 - ph);
-            const uint32_t* o = out + base;
-            for (int q = (int)(((uint32_t)tid - cum) & (kB - 1)); q < ngroups; q += kB) {
-                const int e0 = 4 * q - ph;                  // entry of the group's first slot
-                int id[4], v[4];
+    for (int s = 0; s < kSeg; ++s) {
+        const uint32_t ns = field16(tot, s);
+        if (s < sw) base += ns;
+        if (s == sw) nseg = ns;
+    }
+    {
+        const int n = (int)nseg;
+        const long long g0 = sh_pref[sw];
+        const int ph = (int)(g0 & 3);
+        const int ngroups = (ph + n + 3) >> 2;
+        const int q1 = (ngroups * (part + 1)) / nparts;
+        int* __restrict__ pi = T.arena_idx + (g0 - ph);
+        int16_t* __restrict__ pv = reinterpret_cast<int16_t*>(T.arena_val) + (g0 - ph);
+        const uint32_t* o = out + base;
+        int rabs = 0, rchi = 0;
+        for (int q = (ngroups * part) / nparts + lane; q < q1; q += 32) {
+            const int e0 = 4 * q - ph;                  // entry of the group's first slot
+            int id[4], v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = e0 + k;
+                id[k] = 0;
+                v[k] = 0;
+                if (e >= 0 && e < n) {
+                    const uint32_t w = o[e];
+                    v[k] = (int)__half2short_rn(__ushort_as_half((unsigned short)(w & 0xffffu)));
+                    if constexpr (TOP) {   // position -> vertex index (rows m_0 long)
+                        const int qq = x0 + (int)(w >> 16);
+                        const int yq = (int)fastdiv((uint32_t)qq, divp);
+                        id[k] = yq * m0 + (qq - yq * top_p);
+                    } else {
+                        id[k] = L0 + (int)(w >> 16);
+                    }
+                }
+                rabs += abs(v[k]);
+                rchi += v[k];
+            }
+            if (e0 >= 0 && e0 + 4 <= n) {
+                *reinterpret_cast<int4*>(pi + 4 * q) = make_int4(id[0], id[1], id[2], id[3]);
+                *reinterpret_cast<uint2*>(pv + 4 * q) =
+                    make_uint2(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x5410),
+                               __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x5410));
+            } else {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int e = e0 + k;
-                    id[k] = 0;
-                    v[k] = 0;
                     if (e >= 0 && e < n) {
-                        const uint32_t w = o[e];
-                        v[k] = (int)__half2short_rn(__ushort_as_half((unsigned short)(w & 0xffffu)));
-                        if constexpr (TOP) {   // position -> vertex index (rows m_0 long)
-                            const int q = x0 + (int)(w >> 16);
-                            const int yq = (int)fastdiv((uint32_t)q, divp);
-                            id[k] = yq * m0 + (q - yq * top_p);
-                        } else {
-                            id[k] = L0 + (int)(w >> 16);
-                        }
-                    }
-                    if (s < kNO) red[1 + (s < kNO ? s : 0)] += abs(v[k]);
-                    if (s == 0) red[0] += v[k];
-                }
-                if (e0 >= 0 && e0 + 4 <= n) {
-                    *reinterpret_cast<int4*>(pi + 4 * q) = make_int4(id[0], id[1], id[2], id[3]);
-                    *reinterpret_cast<uint2*>(pv + 4 * q) =
-                        make_uint2(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x5410),
-                                   __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x5410));
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int e = e0 + k;
-                        if (e >= 0 && e < n) {
-                            pi[4 * q + k] = id[k];
-                            pv[4 * q + k] = (int16_t)v[k];
-                        }
+                        pi[4 * q + k] = id[k];
+                        pv[4 * q + k] = (int16_t)v[k];
                     }
                 }
             }
-            base += (uint32_t)n;
-            cum += (uint32_t)ngroups;
         }
-    }
-    // per-warp sums straight to the image totals (no block barrier at the end)
-#pragma unroll
-    for (int i = 0; i <= kNO; ++i) {
-        const int v = (int)__reduce_add_sync(kFull, (unsigned)red[i]);
-        if (lane == 0 && v != 0) {
-            unsigned long long* dst = reinterpret_cast<unsigned long long*>(i == 0 ? &T.chi[b]
-                                                                                 : &T.absum[(long long)b * kNO + i - 1]);
-            atomicAdd(dst, (unsigned long long)(long long)v);
+        // the lower tables' sums straight to the image totals (no block barrier at the end)
+        if (sw < kNO) {   // warp-uniform
+            const int sa = (int)__reduce_add_sync(kFull, (unsigned)rabs);
+            const int sc = (int)__reduce_add_sync(kFull, (unsigned)rchi);
+            if (lane == 0) {
+                if (sa != 0)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&T.absum[(long long)b * kNO + sw]),
+                              (unsigned long long)(long long)sa);
+                if (sw == 0 && sc != 0)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&T.chi[b]), (unsigned long long)(long long)sc);
+            }
         }
     }
 }
