@@ -25,7 +25,6 @@ from itertools import product
 
 import numpy as np
 
-from .oracle import vertex_coords
 
 
 def cells(img: np.ndarray):
@@ -97,6 +96,14 @@ def _complex(img, construction):
     raise ValueError("construction must be 'vertex' or 'top'")
 
 
+def _axis_coords(m: int) -> np.ndarray:
+    """The checker's own copy of the embedding of Section 4.1: m evenly spaced points
+    normalised to [-0.5, 0.5], point i at (2i - (m-1)) / (2(m-1)), each one IEEE division of
+    two exact integers (so it rounds exactly as any other correct evaluation does)."""
+    den = float(2 * (m - 1))
+    return np.array([float(2 * i - (m - 1)) / den for i in range(m)], dtype=np.float64)
+
+
 def vertex_dots(img: np.ndarray, xi, shape=None) -> np.ndarray:
     """<xi, x(v)> for every vertex, in linear order, canonical rounding.  The vertex grid
     has the numpy shape ``shape`` (default: the image's own, vertex construction)."""
@@ -110,7 +117,7 @@ def vertex_dots(img: np.ndarray, xi, shape=None) -> np.ndarray:
     for k in range(n):
         ik = rest % m[k]
         rest //= m[k]
-        p = np.float64(xi[k]) * vertex_coords(m[k])[ik]
+        p = np.float64(xi[k]) * _axis_coords(m[k])[ik]
         s = p if s is None else s + p
     return s
 
