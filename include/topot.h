@@ -170,7 +170,12 @@ TOPOT_API topot_status slab_sum_f64(const double* d_parts, int P, int64_t n, dou
 /* Enqueue the extraction of all tables of `t` from d_pixels on `stream`
  * (asynchronous, no allocation, no host synchronisation: may be captured in a
  * CUDA graph once the handle exists).  Table sizes stay on the device; the
- * evaluation calls read them there.  tables_sync() makes them visible on the host. */
+ * evaluation calls read them there.  tables_sync() makes them visible on the host.
+ * Whole 3-D volumes of 8-bit voxels that are all 0 or 1 (decided on the device at each
+ * build) take a bit-sliced path (Section 3's lower-star values as AND/XOR bit planes);
+ * for such handles the general kernel runs on a stream of the handle, forked from and
+ * joined back to `stream` by events, so the call stays ordered on `stream`.  Tables are
+ * identical whichever path builds them. */
 TOPOT_API topot_status tables_build(topot_tables* t, const void* d_pixels, void* stream);
 
 /* Wait for `stream`, read table sizes, chi and the device error word of `t`.
