@@ -96,3 +96,26 @@ def test_ect_radon_on_binary_tables(tb):
         ref = O.critical_tables(v)
         np.testing.assert_array_equal(e[b], O.ect_grid(ref, dirs, -R, R, 37))
         np.testing.assert_array_equal(r[b], O.radon_grid(ref, dirs, -R, R, 37))
+
+
+def test_captured_graph_follows_new_voxels(tb):
+    """tables_build with the binary path inside a CUDA graph (its side stream is forked and
+    joined within the capture): replays with new voxels, where a binary volume turns grey
+    and a grey one binary, equal the eager results."""
+    shape = (12, 14, 40)
+    vols_a = [synth.grf(shape, 3.0, seed=540, binary=True), synth.grf(shape, 3.0, seed=541)]
+    vols_b = [synth.grf(shape, 3.0, seed=542), synth.grf(shape, 3.0, seed=543, binary=True)]
+    batch_a, batch_b = tb.pack_images(vols_a), tb.pack_images(vols_b)
+    R = synth.image_radius(3)
+    ect_dirs = torch.from_numpy(synth.fibonacci_dirs(64)).cuda()
+    ht_dirs = torch.from_numpy(synth.scale_norms(synth.fibonacci_dirs(96), 9, 0.05, 1.5)).cuda()
+    pipe = tb.Pipeline(batch_a.shapes, batch_a.offsets, batch_a.pixels.numel(), ect=(ect_dirs, -R, R, 48),
+                       hybrid=[("fourier", ht_dirs, "fp32c")])
+    pipe.pixels.copy_(batch_a.pixels)
+    pipe.capture()
+    for batch in (batch_a, batch_b, batch_a):
+        pipe.run(batch.pixels)
+        torch.cuda.synchronize()
+        eager = tb.build_critical_tables(batch)
+        assert torch.equal(pipe.ect_out, tb.ect(eager, ect_dirs, -R, R, 48))
+        assert torch.equal(pipe.hybrid_out[0], tb.hybrid_transform(eager, "fourier", ht_dirs))
