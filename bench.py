@@ -41,7 +41,7 @@ FP64_SAMPLE_DIRS = 128
 # DRAM bytes (read + write) per image of one FP32C hybrid launch: dram__bytes_read.sum +
 # dram__bytes_write.sum of the packed launches in an ncu capture of the 8-image case (the
 # tables are read once per work item, so the traffic grows with the number of images)
-HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.03e6 + 3.71e6) / 8, "ht_fourier": (85.90e6 + 1.19e6) / 8,
+HT_DRAM_BYTES_PER_IMAGE = {"ht_laplace": (84.03e6 + 3.71e6) / 8, "ht_fourier": (86.93e6 + 4.30e6) / 8,
                            "ht_bessel": (96.63e6 + 0.95e6) / 8}
 
 
